@@ -1,0 +1,184 @@
+/*
+ * dmr.h -- C-ABI of the GB300 (sm_103a) evaluator for multi-objective dual
+ * simplex-mesh deformable 3-D image registration (Andreadis, Bosman,
+ * Alderliesten, arXiv 2202.11001).
+ *
+ * One problem = a source and a target image, two tetrahedral meshes with the
+ * same topology (one per image, Sec. 2.1 "dual-dynamic grid"), optional
+ * guidance point pairs (Sec. 2.3.3), and a population of candidate mesh
+ * pairs.  For every candidate the library computes four minimised values,
+ * in this order (FP64):
+ *
+ *   obj[0] f_sim  forward + backward squared intensity difference of
+ *                 corresponding voxels with the black-vs-grey rule, over the
+ *                 total voxel count of both images (Sec. 2.3.1)
+ *   obj[1] f_def  deformation magnitude: Hooke springs on 6 edges + 4 spokes
+ *                 per tetrahedron over 10*N_tet (Sec. 2.3.2, DMR_SPRING), or
+ *                 linear-elastic energy from the deformation gradient with
+ *                 Lame lambda, mu over the total rest volume (DMR_LINEAR)
+ *   obj[2] f_guid symmetric squared distance (mm^2) of guidance pairs carried
+ *                 through their containing tetrahedra, over 2*n_guide
+ *                 (Sec. 2.3.3)
+ *   obj[3] c_fold constraint count: inverted tetrahedra of either mesh,
+ *                 border points that left their border plane (counted once
+ *                 per incident tetrahedron), unlocated guidance points
+ *                 (Sec. 2.3.4); the candidate is feasible iff it is 0
+ *
+ * Conventions
+ *  - Images are [nz][ny][nx], x fastest; voxel (i,j,k) has its centre at
+ *    (i,j,k) in voxel units.  Mesh point (a,b,c) rests at
+ *    -0.5 + a*n/(m-1) per axis, so border points lie on the outer voxel
+ *    faces; border coordinates must stay exactly there.
+ *  - Mesh point id = a + m_x*(b + m_y*c).  Candidate coordinates are FP64,
+ *    [C][2][3][P]: (candidate, mesh 0 = source / 1 = target, axis x/y/z,
+ *    point), in voxel units of that mesh's image.
+ *  - Pointers marked "host or device" may point to either; the library
+ *    asks the CUDA runtime which one it is.  Every input is copied or read
+ *    during the call; the caller keeps ownership of every buffer.
+ *  - Work is enqueued on the problem's stream.  A call that writes to host
+ *    memory synchronises that stream before it returns; a call whose outputs
+ *    are all device pointers returns without waiting.
+ *  - Every call returns DMR_OK or a negative status; no exception crosses
+ *    the ABI.  dmr_last_error() gives the calling thread's last message.
+ */
+#ifndef DMR_H
+#define DMR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmr_problem dmr_problem;
+typedef struct dmr_plan dmr_plan;
+
+enum {
+  DMR_OK = 0,
+  DMR_EINVAL = -1,   /* bad argument or size */
+  DMR_ENOMEM = -2,   /* device or host allocation failed */
+  DMR_ECUDA = -3,    /* a CUDA runtime call failed */
+  DMR_ETIMEOUT = -4, /* reserved: a bounded device wait gave up */
+  DMR_ESTATE = -5    /* call out of order (e.g. commit before eval_partial) */
+};
+
+enum { DMR_F32 = 0, DMR_BF16 = 1, DMR_F16 = 2 };
+enum { DMR_SPRING = 0, DMR_LINEAR = 1 };
+
+typedef struct {
+  const void* img[2];    /* source, target image; host or device */
+  int img_dtype;         /* element type of img[]: DMR_F32 | DMR_BF16 | DMR_F16 */
+  int dims[2][3];        /* (nx, ny, nz) of each image, each >= 1 */
+  double spacing[2][3];  /* mm per voxel of each image, > 0 */
+  int storage_dtype;     /* on-device image type: DMR_F32 | DMR_BF16 | DMR_F16 */
+  int mesh_pts[3];       /* mesh points per axis (both meshes), each >= 2 */
+  const double* guide;   /* [n_guide][2][3] host: source point, target point
+                            (voxel units of their images); NULL if n_guide=0 */
+  int n_guide;
+  int black_rule;        /* 1: a black/grey voxel pair costs 1 (Sec. 2.3.1) */
+  int deform_model;      /* DMR_SPRING (paper) | DMR_LINEAR */
+  double lambda, mu;     /* Lame parameters of DMR_LINEAR */
+  int max_candidates;    /* population capacity, >= 1 */
+  void* stream;          /* cudaStream_t to enqueue on; NULL = default stream */
+} dmr_problem_desc;
+
+/* Create a problem: uploads and converts both images, builds the mirrored
+ * 6-tets-per-cube topology (Sec. 2.1, Fig. 1A/B) and the point -> tet
+ * dependency table (Sec. 2.2).  *out receives a handle the caller frees
+ * with dmr_problem_destroy.  DMR_EINVAL on bad sizes or types. */
+int dmr_problem_create(const dmr_problem_desc* desc, dmr_problem** out);
+int dmr_problem_destroy(dmr_problem* p);
+int dmr_set_stream(dmr_problem* p, void* stream);
+/* n_points = m_x*m_y*m_z, n_tets = 6*(m_x-1)*(m_y-1)*(m_z-1). */
+int dmr_problem_info(const dmr_problem* p, int* n_points, int* n_tets);
+/* Topology copy-out for inspection: tets [N_tet][4] point ids. */
+int dmr_tets_out(const dmr_problem* p, int* tets);
+
+/* Register the family of subsets (FOS) of mesh points that partial
+ * evaluations move together (Sec. 2.2): group g holds the point ids
+ * group_pts[group_ptr[g] .. group_ptr[g+1]) (host arrays, ids distinct
+ * within a group).  The library derives each group's touched tetrahedra
+ * (union of the points' stars) and colours the groups into waves whose
+ * touched sets are pairwise disjoint.  Replaces any earlier FOS. */
+int dmr_set_fos(dmr_problem* p, int n_groups, const int* group_ptr, const int* group_pts);
+/* max_group: largest group size (the G of trial coordinate arrays);
+ * max_touched: largest touched-tet count; n_waves: number of waves. */
+int dmr_fos_info(const dmr_problem* p, int* max_group, int* max_touched, int* n_waves);
+/* wave_ptr [n_waves+1], wave_groups [n_groups] (host). */
+int dmr_fos_waves(const dmr_problem* p, int* wave_ptr, int* wave_groups);
+
+/* Full evaluation (Sec. 2.3) of n_cand candidates; coords [n_cand][2][3][P]
+ * FP64 (host or device); obj_out [n_cand][4] FP64 (host or device).
+ * (Re)initialises the population: candidate c gets these coordinates and
+ * its per-tetrahedron and per-landmark caches.  1 <= n_cand <= capacity. */
+int dmr_eval_full(dmr_problem* p, int n_cand, const double* coords, double* obj_out);
+
+/* Partial evaluation (Sec. 2.2): trial k moves the points of FOS group
+ * group_ids[k] of candidate cand_ids[k] to trial_coords[k] ([2][3][G],
+ * G = max_group, the first |group| entries used) and re-evaluates only the
+ * touched tetrahedra and the guidance points located in them:
+ *   new = stored - sum_{touched} old + sum_{touched} new.
+ * group_ids, cand_ids: [n_trials] (host or device); trial_coords:
+ * [n_trials][2][3][G] FP64 (host or device); obj_out [n_trials][4].
+ * The committed state is unchanged; dmr_commit applies accepted trials. */
+int dmr_eval_partial(dmr_problem* p, int n_trials, const int* group_ids, const int* cand_ids,
+                     const double* trial_coords, double* obj_out);
+
+/* Apply the trials of the last dmr_eval_partial whose accept[k] != 0
+ * ([n_trials] uint8, host or device).  Accepted trials of one candidate must
+ * touch disjoint tetrahedra (their changes are then independent, Sec. 2.2);
+ * otherwise nothing is applied and DMR_EINVAL is returned (checked only
+ * when accept is in host memory).  DMR_ESTATE without a prior partial. */
+int dmr_commit(dmr_problem* p, const uint8_t* accept);
+
+/* Accept-if-improves (Sec. 2.2): on the device, accept trial k iff its
+ * c_fold is lower than the candidate's, or equal and its (f_sim, f_def,
+ * f_guid) weakly Pareto-dominates the candidate's with one strict
+ * improvement; then commit.  accept_out [n_trials] (host, device or NULL).
+ * Accepted trials of one candidate must touch disjoint tetrahedra, which
+ * holds when the trials of the last partial evaluation come from one wave. */
+int dmr_commit_improving(dmr_problem* p, uint8_t* accept_out);
+
+/* Copy-outs of the committed state (outputs host or device). */
+int dmr_objectives_out(dmr_problem* p, int n, const int* cand_ids, double* out /*[n][4]*/);
+int dmr_coords_out(dmr_problem* p, int cand, double* out /*[2][3][P]*/);
+/* Per-tetrahedron voxel coverage counts [N_tet][2] (forward = source
+ * voxels, backward = target voxels) and terms: ssd [N_tet][2], def [N_tet],
+ * fold [N_tet]; any output pointer may be NULL. */
+int dmr_terms_out(dmr_problem* p, int cand, int* cov, double* ssd, double* def, int* fold);
+/* Guidance cache: loc [2][n_guide] (containing tet or -1), term [2][n_guide]. */
+int dmr_landmarks_out(dmr_problem* p, int cand, int* loc, double* term);
+/* Trial k of the last partial evaluation: touched tets (ascending), their
+ * new coverage [n][2], ssd [n][2], def [n], fold [n].  Returns the touched
+ * count (>= 0) or a negative status; outputs may be NULL. */
+int dmr_trial_out(dmr_problem* p, int k, int* tets, int* cov, double* ssd, double* def, int* fold);
+/* Voxel-samples (one per covered voxel per direction) evaluated by the
+ * device since the last reset; reset != 0 zeroes the counter after reading. */
+int dmr_samples(dmr_problem* p, long long* samples, int reset);
+
+/* Generation plan (batched partial evaluation captured in one CUDA graph):
+ * for every wave of the FOS in order, for every candidate in cand_ids:
+ * propose trial = committed coordinates of the group + deltas, evaluate
+ * partially, accept-if-improves, commit.  deltas: [n_groups][n_cand][2][3][G]
+ * FP64 (host or device), copied into the plan.  The plan owns a CUDA graph;
+ * dmr_plan_run launches it on the problem's stream. */
+int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const double* deltas,
+                        dmr_plan** out);
+int dmr_plan_run(dmr_plan* plan);
+int dmr_plan_destroy(dmr_plan* plan);
+
+/* Kernel launches per dmr_plan_run (for accounting). */
+int dmr_plan_launches(const dmr_plan* plan, int* launches);
+
+/* Tile shape of the rasterise-and-sample kernel: warps per CTA (4, 8, 16)
+ * and voxels per warp iteration (32, 64, 128); both 0 = library default. */
+int dmr_set_tile(dmr_problem* p, int warps_per_cta, int voxels_per_warp);
+int dmr_get_tile(const dmr_problem* p, int* warps_per_cta, int* voxels_per_warp);
+
+const char* dmr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMR_H */

@@ -196,6 +196,9 @@ static void tet_vertices(const dmo_problem* pr, const double* c, int mesh, int t
 }
 
 /* Six times the signed volume: e1 . (e2 x e3), e_i = X_i - X_0. */
+/* A tet is valid (unfolded, Sec. 2.3.4) iff 6V is positive and finite. */
+static int vol_ok(double v) { return v > 0 && isfinite(v); }
+
 static double six_vol(const double X[4][3]) {
   double e[3][3], r[3];
   for (int i = 0; i < 3; ++i)
@@ -433,7 +436,7 @@ static void tet_terms(const dmo_problem* pr, const double* c, int t, dmo_term* o
   double vol6[2] = {six_vol(X[0]), six_vol(X[1])};
   int fold = 0;
   for (int k = 0; k < 2; ++k)
-    if (!(vol6[k] > 0)) ++fold;
+    if (!vol_ok(vol6[k])) ++fold;
   for (int i = 0; i < 4; ++i)
     for (int k = 0; k < 2; ++k) fold += border_violations(pr, c, k, pr->tet[4 * t + i]);
   out->fold = fold;
@@ -441,7 +444,7 @@ static void tet_terms(const dmo_problem* pr, const double* c, int t, dmo_term* o
   for (int d = 0; d < 2; ++d) {
     out->ssd[d] = 0.0;
     out->cov[d] = 0;
-    if (!(vol6[d] > 0)) continue;
+    if (!vol_ok(vol6[d])) continue;
     const double(*own)[3] = X[d];
     const double(*par)[3] = X[1 - d];
     const int* n = pr->n[d];
@@ -499,7 +502,7 @@ static int locate(const dmo_problem* pr, const double* c, int mesh, const double
     int t = list ? list[k] : k;
     double X[4][3];
     tet_vertices(pr, c, mesh, t, X);
-    if (!(six_vol(X) > 0)) continue;
+    if (!vol_ok(six_vol(X))) continue;
     dmo_face F[4];
     tet_faces(pr, t, X, F);
     if (inside_faces(F, p)) return t;
@@ -994,7 +997,7 @@ int dmo_inside(void* h, int mesh, const double* coords, int t, const double* p) 
   dmo_problem* pr = (dmo_problem*)h;
   double X[4][3];
   tet_vertices(pr, coords, mesh, t, X);
-  if (!(six_vol(X) > 0)) return 0;
+  if (!vol_ok(six_vol(X))) return 0;
   dmo_face F[4];
   tet_faces(pr, t, X, F);
   return inside_faces(F, p);
@@ -1007,7 +1010,7 @@ void dmo_coverage_mask(void* h, int mesh, const double* coords, int t, uint8_t* 
   const int* n = pr->n[mesh];
   double X[4][3];
   tet_vertices(pr, coords, mesh, t, X);
-  int ok = six_vol(X) > 0;
+  int ok = vol_ok(six_vol(X));
   dmo_face F[4];
   tet_faces(pr, t, X, F);
   for (int z = 0; z < n[2]; ++z)

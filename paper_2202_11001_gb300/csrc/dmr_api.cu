@@ -1,0 +1,1112 @@
+// Host side of the C-ABI declared in include/dmr.h: problem lifecycle,
+// mesh topology (Sec. 2.1), FOS registration and wave colouring (Sec. 2.2),
+// and the orchestration of full / partial evaluation, commit and the
+// CUDA-graph generation plan.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dmr.h"
+#include "dmr_internal.cuh"
+
+using namespace dmr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(DMR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(DMR_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return DMR_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+size_t dtype_size(int dt) { return dt == DMR_F32 ? 4 : 2; }
+
+// Scratch for one batch of (trial, tet) pairs.
+struct Scratch {
+  int cap_tt = 0, cap_tr = 0, gmax = 0, aff_cap = 0;
+  ItemRec* rec = nullptr;
+  double* o_ssd = nullptr;
+  int* o_cov = nullptr;
+  double* o_def = nullptr;
+  int* o_fold = nullptr;
+  int* tt_trial = nullptr;
+  int* tt_tet = nullptr;
+  uint32_t* tt_slot = nullptr;
+  int* tr_cand = nullptr;
+  int* tr_first = nullptr;
+  int* tr_ntt = nullptr;
+  int* tr_group = nullptr;
+  double* tr_coords = nullptr;
+  int* aff_n = nullptr;
+  int* aff_idx = nullptr;
+  int* aff_loc = nullptr;
+  double* aff_term = nullptr;
+  double* tr_delta = nullptr;
+  double* tr_obj = nullptr;
+  uint8_t* accept = nullptr;
+  int* cand_ptr = nullptr;
+  int* cand_trials = nullptr;
+  unsigned* work = nullptr;
+
+  void release() {
+    dfree(rec); dfree(o_ssd); dfree(o_cov); dfree(o_def); dfree(o_fold);
+    dfree(tt_trial); dfree(tt_tet); dfree(tt_slot);
+    dfree(tr_cand); dfree(tr_first); dfree(tr_ntt); dfree(tr_group); dfree(tr_coords);
+    dfree(aff_n); dfree(aff_idx); dfree(aff_loc); dfree(aff_term);
+    dfree(tr_delta); dfree(tr_obj); dfree(accept); dfree(cand_ptr); dfree(cand_trials); dfree(work);
+    cap_tt = cap_tr = 0;
+  }
+
+  int ensure(int ntt, int ntr, int gm, int acap) {
+    if (ntt <= cap_tt && ntr <= cap_tr && gm <= gmax && acap <= aff_cap) return DMR_OK;
+    int nt = std::max(ntt, cap_tt), nr = std::max(ntr, cap_tr), g = std::max(gm, gmax), a = std::max(acap, aff_cap);
+    release();
+    int rc = DMR_OK;
+    if ((rc = dalloc(&rec, 2 * (size_t)nt)) || (rc = dalloc(&o_ssd, 2 * (size_t)nt)) ||
+        (rc = dalloc(&o_cov, 2 * (size_t)nt)) || (rc = dalloc(&o_def, (size_t)nt)) ||
+        (rc = dalloc(&o_fold, (size_t)nt)) || (rc = dalloc(&tt_trial, (size_t)nt)) ||
+        (rc = dalloc(&tt_tet, (size_t)nt)) || (rc = dalloc(&tt_slot, (size_t)nt)) ||
+        (rc = dalloc(&tr_cand, (size_t)nr)) || (rc = dalloc(&tr_first, (size_t)nr)) ||
+        (rc = dalloc(&tr_ntt, (size_t)nr)) || (rc = dalloc(&tr_group, (size_t)nr)) ||
+        (rc = dalloc(&tr_coords, (size_t)nr * 6 * std::max(g, 1))) || (rc = dalloc(&aff_n, (size_t)nr)) ||
+        (rc = dalloc(&aff_idx, (size_t)nr * std::max(a, 1))) || (rc = dalloc(&aff_loc, (size_t)nr * std::max(a, 1))) ||
+        (rc = dalloc(&aff_term, (size_t)nr * std::max(a, 1))) || (rc = dalloc(&tr_delta, (size_t)nr * 4)) ||
+        (rc = dalloc(&tr_obj, (size_t)nr * 4)) || (rc = dalloc(&accept, (size_t)nr)) ||
+        (rc = dalloc(&cand_ptr, (size_t)nr + 1)) || (rc = dalloc(&cand_trials, (size_t)nr)) ||
+        (rc = dalloc(&work, 1))) {
+      release();
+      return rc;
+    }
+    cap_tt = nt;
+    cap_tr = nr;
+    gmax = g;
+    aff_cap = a;
+    return DMR_OK;
+  }
+};
+
+}  // namespace
+
+struct dmr_problem {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  int n_sm = 1;
+  int P = 0, ntet = 0, m[3] = {0, 0, 0};
+  int n[2][3];
+  double sp[2][3];
+  int storage = DMR_F32;
+  int black_rule = 1, model = DMR_SPRING;
+  double lam = 1, mu = 1;
+  int ng = 0;
+  int cap = 0, C = 0;
+  std::vector<int> tets;
+  std::vector<uint32_t> fperm;
+  std::vector<uint8_t> fixmask;
+  std::vector<int> star_ptr, star;
+  std::vector<double> guide;
+  // device state
+  void* plain[2] = {nullptr, nullptr};
+  void* cells[2] = {nullptr, nullptr};
+  uint8_t* cflag[2] = {nullptr, nullptr};
+  int4* d_tet = nullptr;
+  uint32_t* d_fperm = nullptr;
+  uint8_t* d_fix = nullptr;
+  float* d_restvol = nullptr;
+  double* d_guide = nullptr;
+  double* d_coords = nullptr;
+  double* d_ssd = nullptr;
+  int* d_cov = nullptr;
+  double* d_def = nullptr;
+  int* d_fold = nullptr;
+  int* d_loc = nullptr;
+  double* d_gterm = nullptr;
+  double* d_sums = nullptr;
+  unsigned long long* d_samples = nullptr;
+  DevProblem hp;
+  DevProblem* d_prob = nullptr;
+  double* d_obj = nullptr;  // [cap][4] staging for objective outputs
+  // FOS
+  int n_groups = 0, gmax = 0, max_touched = 0;
+  std::vector<int> g_ptr, g_pts, g_tptr, g_tets, wave_ptr, wave_groups;
+  std::vector<uint32_t> g_slot;
+  int* d_gptr = nullptr;
+  int* d_gpts = nullptr;
+  // scratch and last partial evaluation
+  Scratch sc;
+  bool have_partial = false, partial_safe = false;
+  int last_ntr = 0, last_ntt = 0;
+  std::vector<int> last_cand, last_group, last_first, last_ntt_v;
+  int last_nlist = 0;
+  int warps = 8, vpw = 32;
+};
+
+struct dmr_plan {
+  dmr_problem* p = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+  // all waves' arrays (device), owned by the plan
+  int* tt_trial = nullptr;
+  int* tt_tet = nullptr;
+  uint32_t* tt_slot = nullptr;
+  int* tr_cand = nullptr;
+  int* tr_first = nullptr;
+  int* tr_ntt = nullptr;
+  int* tr_group = nullptr;
+  double* deltas = nullptr;
+  int* cand_ptr = nullptr;
+  int* cand_trials = nullptr;
+  Scratch sc;  // per-wave scratch (largest wave)
+};
+
+// ------------------------------------------------------------ topology
+namespace {
+
+const int kAxisOrder[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// Mirrored 6-tets-per-cube lattice (Sec. 2.1, Fig. 1A/B): each cube is cut
+// along the diagonal from its even-index corner to its odd-index corner; the
+// 6 tets follow the 6 axis orders along it; orientation made positive.
+void build_topology(dmr_problem* p) {
+  const int mx = p->m[0], my = p->m[1], mz = p->m[2];
+  p->P = mx * my * mz;
+  p->ntet = 6 * (mx - 1) * (my - 1) * (mz - 1);
+  p->tets.assign(4 * (size_t)p->ntet, 0);
+  p->fperm.assign(p->ntet, 0u);
+  auto pid = [&](int a, int b, int c) { return a + mx * (b + my * c); };
+  int t = 0;
+  for (int cz = 0; cz < mz - 1; ++cz)
+    for (int cy = 0; cy < my - 1; ++cy)
+      for (int cx = 0; cx < mx - 1; ++cx) {
+        int cube[3] = {cx, cy, cz}, s0[3], dir[3];
+        for (int k = 0; k < 3; ++k) {
+          s0[k] = cube[k] + (cube[k] & 1);
+          dir[k] = (cube[k] & 1) ? -1 : 1;
+        }
+        for (int q = 0; q < 6; ++q, ++t) {
+          int v[4][3];
+          for (int k = 0; k < 3; ++k) v[0][k] = s0[k];
+          for (int s = 0; s < 3; ++s) {
+            for (int k = 0; k < 3; ++k) v[s + 1][k] = v[s][k];
+            v[s + 1][kAxisOrder[q][s]] += dir[kAxisOrder[q][s]];
+          }
+          long a[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) a[i][k] = v[i + 1][k] - v[0][k];
+          long det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                     a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+          int id[4];
+          for (int i = 0; i < 4; ++i) id[i] = pid(v[i][0], v[i][1], v[i][2]);
+          if (det < 0) std::swap(id[1], id[2]);
+          for (int i = 0; i < 4; ++i) p->tets[4 * (size_t)t + i] = id[i];
+          // faces: canonical vertex order and inward sign
+          uint32_t packed = 0;
+          for (int f = 0; f < 4; ++f) {
+            int l[3], k = 0;
+            for (int i = 0; i < 4; ++i)
+              if (i != f) l[k++] = i;
+            std::sort(l, l + 3, [&](int x, int y) { return id[x] < id[y]; });
+            int perm[4] = {l[0], l[1], l[2], f}, inv = 0;
+            for (int i = 0; i < 4; ++i)
+              for (int j = i + 1; j < 4; ++j)
+                if (perm[i] > perm[j]) ++inv;
+            uint32_t byte = (uint32_t)l[0] | ((uint32_t)l[1] << 2) | ((uint32_t)l[2] << 4) | ((uint32_t)(inv & 1) << 6);
+            packed |= byte << (8 * f);
+          }
+          p->fperm[t] = packed;
+        }
+      }
+  p->star_ptr.assign(p->P + 1, 0);
+  for (int tt = 0; tt < p->ntet; ++tt)
+    for (int i = 0; i < 4; ++i) p->star_ptr[p->tets[4 * (size_t)tt + i] + 1]++;
+  for (int v = 0; v < p->P; ++v) p->star_ptr[v + 1] += p->star_ptr[v];
+  p->star.assign(4 * (size_t)p->ntet, 0);
+  std::vector<int> fill(p->star_ptr.begin(), p->star_ptr.end() - 1);
+  for (int tt = 0; tt < p->ntet; ++tt)
+    for (int i = 0; i < 4; ++i) p->star[fill[p->tets[4 * (size_t)tt + i]]++] = tt;
+  p->fixmask.assign(p->P, 0);
+  for (int c = 0; c < mz; ++c)
+    for (int b = 0; b < my; ++b)
+      for (int a = 0; a < mx; ++a) {
+        int idx[3] = {a, b, c};
+        uint8_t fm = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+          if (idx[ax] == 0) fm |= (uint8_t)(1 << ax);
+          if (idx[ax] == p->m[ax] - 1) fm |= (uint8_t)((1 << ax) | (1 << (3 + ax)));
+        }
+        p->fixmask[pid(a, b, c)] = fm;
+      }
+}
+
+void release_problem(dmr_problem* p) {
+  for (int k = 0; k < 2; ++k) {
+    dfree(p->plain[k]);
+    dfree(p->cells[k]);
+    dfree(p->cflag[k]);
+  }
+  dfree(p->d_tet); dfree(p->d_fperm); dfree(p->d_fix); dfree(p->d_restvol); dfree(p->d_guide);
+  dfree(p->d_coords); dfree(p->d_ssd); dfree(p->d_cov); dfree(p->d_def); dfree(p->d_fold);
+  dfree(p->d_loc); dfree(p->d_gterm); dfree(p->d_sums); dfree(p->d_samples); dfree(p->d_prob); dfree(p->d_obj);
+  dfree(p->d_gptr); dfree(p->d_gpts);
+  p->sc.release();
+}
+
+int upload_prob(dmr_problem* p) {
+  CU(cudaMemcpyAsync(p->d_prob, &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice, p->st));
+  return DMR_OK;
+}
+
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st, bool& host_dst) {
+  host_dst = !is_device_ptr(dst);
+  CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+  return DMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dmr_last_error(void) { return g_err.c_str(); }
+
+int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
+  if (!d || !out) return fail(DMR_EINVAL, "null argument");
+  *out = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (!d->img[k]) return fail(DMR_EINVAL, "image pointer is null");
+    for (int a = 0; a < 3; ++a) {
+      if (d->dims[k][a] < 1 || d->dims[k][a] > (1 << 20)) return fail(DMR_EINVAL, "image dims out of range");
+      if (!(d->spacing[k][a] > 0) || !std::isfinite(d->spacing[k][a])) return fail(DMR_EINVAL, "spacing must be > 0");
+    }
+    if ((long)(d->dims[k][0] + 2) * (d->dims[k][1] + 2) * (d->dims[k][2] + 2) > (1L << 31))
+      return fail(DMR_EINVAL, "image too large");
+  }
+  for (int a = 0; a < 3; ++a)
+    if (d->mesh_pts[a] < 2 || d->mesh_pts[a] > 4096) return fail(DMR_EINVAL, "mesh_pts must be >= 2");
+  if ((long)d->mesh_pts[0] * d->mesh_pts[1] * d->mesh_pts[2] > (1L << 24)) return fail(DMR_EINVAL, "mesh too large");
+  if (d->img_dtype < 0 || d->img_dtype > 2 || d->storage_dtype < 0 || d->storage_dtype > 2)
+    return fail(DMR_EINVAL, "bad dtype");
+  if (d->deform_model != DMR_SPRING && d->deform_model != DMR_LINEAR) return fail(DMR_EINVAL, "bad deform_model");
+  if (d->n_guide < 0 || (d->n_guide > 0 && !d->guide)) return fail(DMR_EINVAL, "bad guidance arguments");
+  if (d->max_candidates < 1) return fail(DMR_EINVAL, "max_candidates must be >= 1");
+  dmr_problem* p = new (std::nothrow) dmr_problem();
+  if (!p) return fail(DMR_ENOMEM, "host allocation failed");
+  int rc = DMR_OK;
+  cudaGetDevice(&p->dev);
+  cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->dev);
+  p->st = (cudaStream_t)d->stream;
+  for (int k = 0; k < 2; ++k)
+    for (int a = 0; a < 3; ++a) {
+      p->n[k][a] = d->dims[k][a];
+      p->sp[k][a] = d->spacing[k][a];
+    }
+  for (int a = 0; a < 3; ++a) p->m[a] = d->mesh_pts[a];
+  p->storage = d->storage_dtype;
+  p->black_rule = d->black_rule;
+  p->model = d->deform_model;
+  p->lam = d->lambda;
+  p->mu = d->mu;
+  p->ng = d->n_guide;
+  p->cap = d->max_candidates;
+  p->guide.assign(d->guide ? d->guide : (const double*)nullptr, d->guide ? d->guide + 6 * (size_t)p->ng : nullptr);
+  for (double g : p->guide)
+    if (!std::isfinite(g)) {
+      delete p;
+      return fail(DMR_EINVAL, "non-finite guidance coordinate");
+    }
+  build_topology(p);
+  // images: input -> storage, plain + corner-packed cells
+  for (int k = 0; k < 2; ++k) {
+    long nv = (long)p->n[k][0] * p->n[k][1] * p->n[k][2];
+    long nc = (long)(p->n[k][0] + 2) * (p->n[k][1] + 2) * (p->n[k][2] + 2);
+    if ((rc = dalloc((char**)&p->plain[k], nv * dtype_size(p->storage)))) goto fail_;
+    if ((rc = dalloc((char**)&p->cells[k], nc * 8 * dtype_size(p->storage)))) goto fail_;
+    if ((rc = dalloc(&p->cflag[k], nc))) goto fail_;
+    void* src = (void*)d->img[k];
+    void* tmp = nullptr;
+    if (!is_device_ptr(src)) {
+      if ((rc = dalloc((char**)&tmp, nv * dtype_size(d->img_dtype)))) goto fail_;
+      cudaMemcpyAsync(tmp, src, nv * dtype_size(d->img_dtype), cudaMemcpyHostToDevice, p->st);
+      src = tmp;
+    }
+    launch_convert_image(src, d->img_dtype, p->plain[k], p->storage, nv, p->st);
+    launch_build_cells(p->plain[k], p->storage, p->n[k], p->cells[k], p->cflag[k], p->st);
+    if (tmp) {
+      cudaStreamSynchronize(p->st);
+      cudaFree(tmp);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = fail(DMR_ECUDA, "image preparation failed");
+      goto fail_;
+    }
+  }
+  {
+    // topology + rest volumes
+    std::vector<int4> t4(p->ntet);
+    for (int t = 0; t < p->ntet; ++t)
+      t4[t] = make_int4(p->tets[4 * t], p->tets[4 * t + 1], p->tets[4 * t + 2], p->tets[4 * t + 3]);
+    std::vector<float> rv(p->ntet);
+    for (int t = 0; t < p->ntet; ++t) {
+      double X[4][3];
+      for (int i = 0; i < 4; ++i) {
+        int v = p->tets[4 * t + i];
+        int idx[3] = {v % p->m[0], (v / p->m[0]) % p->m[1], v / (p->m[0] * p->m[1])};
+        for (int a = 0; a < 3; ++a)
+          X[i][a] = ((double)idx[a] * (double)p->n[0][a] / (double)(p->m[a] - 1) - 0.5) * p->sp[0][a];
+      }
+      double e[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) e[i][a] = X[i + 1][a] - X[0][a];
+      double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                   e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+      rv[t] = (float)(std::fabs(det) / 6.0);
+    }
+    double rvs = 0;
+    for (int t = 0; t < p->ntet; ++t) {
+      double X[4][3];
+      for (int i = 0; i < 4; ++i) {
+        int v = p->tets[4 * t + i];
+        int idx[3] = {v % p->m[0], (v / p->m[0]) % p->m[1], v / (p->m[0] * p->m[1])};
+        for (int a = 0; a < 3; ++a)
+          X[i][a] = ((double)idx[a] * (double)p->n[0][a] / (double)(p->m[a] - 1) - 0.5) * p->sp[0][a];
+      }
+      double e[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) e[i][a] = X[i + 1][a] - X[0][a];
+      double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                   e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+      rvs += std::fabs(det) / 6.0;
+    }
+    size_t C = p->cap;
+    if ((rc = dalloc(&p->d_tet, p->ntet)) || (rc = dalloc(&p->d_fperm, p->ntet)) || (rc = dalloc(&p->d_fix, p->P)) ||
+        (rc = dalloc(&p->d_restvol, p->ntet)) || (rc = dalloc(&p->d_guide, std::max<size_t>(1, p->guide.size()))) ||
+        (rc = dalloc(&p->d_coords, C * 6 * p->P)) || (rc = dalloc(&p->d_ssd, C * p->ntet * 2)) ||
+        (rc = dalloc(&p->d_cov, C * p->ntet * 2)) || (rc = dalloc(&p->d_def, C * p->ntet)) ||
+        (rc = dalloc(&p->d_fold, C * p->ntet)) || (rc = dalloc(&p->d_loc, C * 2 * std::max(1, p->ng))) ||
+        (rc = dalloc(&p->d_gterm, C * 2 * std::max(1, p->ng))) || (rc = dalloc(&p->d_sums, C * 4)) ||
+        (rc = dalloc(&p->d_samples, 1)) || (rc = dalloc(&p->d_prob, 1)) || (rc = dalloc(&p->d_obj, C * 4)))
+      goto fail_;
+    cudaMemcpyAsync(p->d_tet, t4.data(), sizeof(int4) * p->ntet, cudaMemcpyHostToDevice, p->st);
+    cudaMemcpyAsync(p->d_fperm, p->fperm.data(), sizeof(uint32_t) * p->ntet, cudaMemcpyHostToDevice, p->st);
+    cudaMemcpyAsync(p->d_fix, p->fixmask.data(), p->P, cudaMemcpyHostToDevice, p->st);
+    cudaMemcpyAsync(p->d_restvol, rv.data(), sizeof(float) * p->ntet, cudaMemcpyHostToDevice, p->st);
+    if (p->ng)
+      cudaMemcpyAsync(p->d_guide, p->guide.data(), sizeof(double) * p->guide.size(), cudaMemcpyHostToDevice, p->st);
+    cudaMemsetAsync(p->d_samples, 0, sizeof(unsigned long long), p->st);
+    DevProblem& h = p->hp;
+    memset(&h, 0, sizeof(h));
+    for (int k = 0; k < 2; ++k) {
+      h.plain[k] = p->plain[k];
+      h.cells[k] = p->cells[k];
+      h.cflag[k] = p->cflag[k];
+      for (int a = 0; a < 3; ++a) {
+        h.n[k][a] = p->n[k][a];
+        h.spd[k][a] = p->sp[k][a];
+        h.sp[k][a] = (float)p->sp[k][a];
+      }
+    }
+    h.dtype = p->storage;
+    h.P = p->P;
+    h.ntet = p->ntet;
+    for (int a = 0; a < 3; ++a) h.m[a] = p->m[a];
+    h.tet = p->d_tet;
+    h.fperm = p->d_fperm;
+    h.fixmask = p->d_fix;
+    h.rest_vol = p->d_restvol;
+    h.black_rule = p->black_rule;
+    h.model = p->model;
+    h.lam = (float)p->lam;
+    h.mu = (float)p->mu;
+    h.sim_norm = (double)p->n[0][0] * p->n[0][1] * p->n[0][2] + (double)p->n[1][0] * p->n[1][1] * p->n[1][2];
+    h.def_norm = p->model == DMR_LINEAR ? rvs : 10.0 * p->ntet;
+    h.guid_norm = 2.0 * std::max(1, p->ng);
+    h.ng = p->ng;
+    h.guide = p->d_guide;
+    h.C = 0;
+    h.coords = p->d_coords;
+    h.c_ssd = p->d_ssd;
+    h.c_cov = p->d_cov;
+    h.c_def = p->d_def;
+    h.c_fold = p->d_fold;
+    h.c_loc = p->d_loc;
+    h.c_gterm = p->d_gterm;
+    h.sums = p->d_sums;
+    h.samples = p->d_samples;
+    if ((rc = upload_prob(p))) goto fail_;
+    cudaError_t e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) {
+      rc = fail(DMR_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+      goto fail_;
+    }
+  }
+  *out = p;
+  return DMR_OK;
+fail_:
+  release_problem(p);
+  delete p;
+  return rc;
+}
+
+int dmr_problem_destroy(dmr_problem* p) {
+  if (!p) return DMR_OK;
+  cudaStreamSynchronize(p->st);
+  release_problem(p);
+  delete p;
+  return DMR_OK;
+}
+
+int dmr_set_stream(dmr_problem* p, void* stream) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  p->st = (cudaStream_t)stream;
+  return DMR_OK;
+}
+
+int dmr_problem_info(const dmr_problem* p, int* n_points, int* n_tets) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (n_points) *n_points = p->P;
+  if (n_tets) *n_tets = p->ntet;
+  return DMR_OK;
+}
+
+int dmr_tets_out(const dmr_problem* p, int* tets) {
+  if (!p || !tets) return fail(DMR_EINVAL, "null argument");
+  memcpy(tets, p->tets.data(), sizeof(int) * 4 * (size_t)p->ntet);
+  return DMR_OK;
+}
+
+int dmr_set_tile(dmr_problem* p, int warps_per_cta, int voxels_per_warp) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (warps_per_cta == 0) warps_per_cta = 8;
+  if (voxels_per_warp == 0) voxels_per_warp = 32;
+  if (warps_per_cta != 4 && warps_per_cta != 8 && warps_per_cta != 16) return fail(DMR_EINVAL, "warps_per_cta");
+  if (voxels_per_warp != 32 && voxels_per_warp != 64 && voxels_per_warp != 128) return fail(DMR_EINVAL, "voxels_per_warp");
+  p->warps = warps_per_cta;
+  p->vpw = voxels_per_warp;
+  return DMR_OK;
+}
+
+int dmr_get_tile(const dmr_problem* p, int* w, int* v) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (w) *w = p->warps;
+  if (v) *v = p->vpw;
+  return DMR_OK;
+}
+
+// ------------------------------------------------------------ FOS
+int dmr_set_fos(dmr_problem* p, int n_groups, const int* group_ptr, const int* group_pts) {
+  if (!p || n_groups < 1 || !group_ptr || !group_pts) return fail(DMR_EINVAL, "bad FOS arguments");
+  if (group_ptr[0] != 0) return fail(DMR_EINVAL, "group_ptr[0] must be 0");
+  std::vector<int> gp(group_ptr, group_ptr + n_groups + 1);
+  int gmax = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    int sz = gp[g + 1] - gp[g];
+    if (sz < 1 || sz > 254) return fail(DMR_EINVAL, "group sizes must be 1..254");
+    gmax = std::max(gmax, sz);
+  }
+  std::vector<int> pts(group_pts, group_pts + gp[n_groups]);
+  for (int v : pts)
+    if (v < 0 || v >= p->P) return fail(DMR_EINVAL, "group point id out of range");
+  // touched sets and per-vertex slots
+  std::vector<int> tptr(n_groups + 1, 0), tl;
+  std::vector<uint32_t> slot;
+  std::vector<int> mark(p->ntet, -1);
+  int maxt = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    std::vector<int> ts;
+    for (int j = gp[g]; j < gp[g + 1]; ++j) {
+      int v = pts[j];
+      for (int q = gp[g]; q < j; ++q)
+        if (pts[q] == v) return fail(DMR_EINVAL, "duplicate point in a group");
+      for (int s = p->star_ptr[v]; s < p->star_ptr[v + 1]; ++s)
+        if (mark[p->star[s]] != g) {
+          mark[p->star[s]] = g;
+          ts.push_back(p->star[s]);
+        }
+    }
+    std::sort(ts.begin(), ts.end());
+    for (int t : ts) {
+      uint32_t sl = 0;
+      for (int i = 0; i < 4; ++i) {
+        int v = p->tets[4 * (size_t)t + i];
+        for (int j = gp[g]; j < gp[g + 1]; ++j)
+          if (pts[j] == v) sl |= (uint32_t)(j - gp[g] + 1) << (8 * i);
+      }
+      tl.push_back(t);
+      slot.push_back(sl);
+    }
+    tptr[g + 1] = (int)tl.size();
+    maxt = std::max(maxt, (int)ts.size());
+  }
+  // greedy colouring: groups in one wave touch disjoint tets
+  std::vector<int> color(n_groups, -1), tet_last(p->ntet, -1);
+  std::vector<std::vector<int>> waves;
+  std::vector<std::vector<char>> used;  // per wave: tets used
+  for (int g = 0; g < n_groups; ++g) {
+    int w = 0;
+    for (;; ++w) {
+      if (w == (int)waves.size()) {
+        waves.emplace_back();
+        used.emplace_back(p->ntet, 0);
+      }
+      bool ok = true;
+      for (int j = tptr[g]; j < tptr[g + 1] && ok; ++j)
+        if (used[w][tl[j]]) ok = false;
+      if (ok) break;
+    }
+    for (int j = tptr[g]; j < tptr[g + 1]; ++j) used[w][tl[j]] = 1;
+    waves[w].push_back(g);
+    color[g] = w;
+  }
+  p->wave_ptr.assign(1, 0);
+  p->wave_groups.clear();
+  for (auto& w : waves) {
+    p->wave_groups.insert(p->wave_groups.end(), w.begin(), w.end());
+    p->wave_ptr.push_back((int)p->wave_groups.size());
+  }
+  p->n_groups = n_groups;
+  p->gmax = gmax;
+  p->max_touched = maxt;
+  p->g_ptr = gp;
+  p->g_pts = pts;
+  p->g_tptr = tptr;
+  p->g_tets = tl;
+  p->g_slot = slot;
+  dfree(p->d_gptr);
+  dfree(p->d_gpts);
+  int rc;
+  if ((rc = dalloc(&p->d_gptr, gp.size())) || (rc = dalloc(&p->d_gpts, pts.size()))) return rc;
+  CU(cudaMemcpyAsync(p->d_gptr, gp.data(), sizeof(int) * gp.size(), cudaMemcpyHostToDevice, p->st));
+  CU(cudaMemcpyAsync(p->d_gpts, pts.data(), sizeof(int) * pts.size(), cudaMemcpyHostToDevice, p->st));
+  CU(cudaStreamSynchronize(p->st));
+  p->have_partial = false;
+  return DMR_OK;
+}
+
+int dmr_fos_info(const dmr_problem* p, int* max_group, int* max_touched, int* n_waves) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (p->n_groups == 0) return fail(DMR_ESTATE, "no FOS registered");
+  if (max_group) *max_group = p->gmax;
+  if (max_touched) *max_touched = p->max_touched;
+  if (n_waves) *n_waves = (int)p->wave_ptr.size() - 1;
+  return DMR_OK;
+}
+
+int dmr_fos_waves(const dmr_problem* p, int* wave_ptr, int* wave_groups) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (p->n_groups == 0) return fail(DMR_ESTATE, "no FOS registered");
+  if (wave_ptr) memcpy(wave_ptr, p->wave_ptr.data(), sizeof(int) * p->wave_ptr.size());
+  if (wave_groups) memcpy(wave_groups, p->wave_groups.data(), sizeof(int) * p->wave_groups.size());
+  return DMR_OK;
+}
+
+// ------------------------------------------------------------ evaluation
+namespace {
+
+Batch make_batch(dmr_problem* p, Scratch& s, int n_tt, int n_tr) {
+  Batch b;
+  memset(&b, 0, sizeof(b));
+  b.n_tt = n_tt;
+  b.tt_trial = s.tt_trial;
+  b.tt_tet = s.tt_tet;
+  b.tt_slot = s.tt_slot;
+  b.n_trials = n_tr;
+  b.tr_prob = nullptr;
+  b.tr_cand = s.tr_cand;
+  b.tr_first = s.tr_first;
+  b.tr_ntt = s.tr_ntt;
+  b.tr_coords = s.tr_coords;
+  b.gmax = std::max(1, p->gmax);
+  b.rec = s.rec;
+  b.o_ssd = s.o_ssd;
+  b.o_cov = s.o_cov;
+  b.o_def = s.o_def;
+  b.o_fold = s.o_fold;
+  b.work = s.work;
+  b.aff_cap = s.aff_cap;
+  b.aff_n = p->ng > 0 ? s.aff_n : nullptr;
+  b.aff_idx = s.aff_idx;
+  b.aff_loc = s.aff_loc;
+  b.aff_term = s.aff_term;
+  b.tr_delta = s.tr_delta;
+  b.tr_obj = s.tr_obj;
+  return b;
+}
+
+}  // namespace
+
+int dmr_eval_full(dmr_problem* p, int n_cand, const double* coords, double* obj_out) {
+  if (!p || !coords || !obj_out) return fail(DMR_EINVAL, "null argument");
+  if (n_cand < 1 || n_cand > p->cap) return fail(DMR_EINVAL, "n_cand out of range");
+  p->have_partial = false;
+  size_t csz = (size_t)6 * p->P;
+  CU(cudaMemcpyAsync(p->d_coords, coords, sizeof(double) * csz * n_cand, cudaMemcpyDefault, p->st));
+  p->C = n_cand;
+  p->hp.C = n_cand;
+  int rc;
+  if ((rc = upload_prob(p))) return rc;
+  const int chunk_tt_cap = 1 << 20;
+  int cpc = std::max(1, std::min(n_cand, chunk_tt_cap / std::max(1, p->ntet)));
+  if ((rc = p->sc.ensure(cpc * p->ntet, cpc, std::max(1, p->gmax), 2 * std::max(1, p->ng)))) return rc;
+  std::vector<int> tt_trial((size_t)cpc * p->ntet), tt_tet((size_t)cpc * p->ntet), tr_cand(cpc), tr_first(cpc),
+      tr_ntt(cpc);
+  for (int c0 = 0; c0 < n_cand; c0 += cpc) {
+    int nc = std::min(cpc, n_cand - c0);
+    for (int ci = 0; ci < nc; ++ci) {
+      tr_cand[ci] = c0 + ci;
+      tr_first[ci] = ci * p->ntet;
+      tr_ntt[ci] = p->ntet;
+      for (int t = 0; t < p->ntet; ++t) {
+        tt_trial[(size_t)ci * p->ntet + t] = ci;
+        tt_tet[(size_t)ci * p->ntet + t] = t;
+      }
+    }
+    int ntt = nc * p->ntet;
+    CU(cudaMemcpyAsync(p->sc.tt_trial, tt_trial.data(), sizeof(int) * ntt, cudaMemcpyHostToDevice, p->st));
+    CU(cudaMemcpyAsync(p->sc.tt_tet, tt_tet.data(), sizeof(int) * ntt, cudaMemcpyHostToDevice, p->st));
+    CU(cudaMemcpyAsync(p->sc.tr_cand, tr_cand.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, p->st));
+    CU(cudaMemcpyAsync(p->sc.tr_first, tr_first.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, p->st));
+    CU(cudaMemcpyAsync(p->sc.tr_ntt, tr_ntt.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, p->st));
+    Batch b = make_batch(p, p->sc, ntt, nc);
+    b.tt_slot = nullptr;
+    b.tr_coords = nullptr;
+    size_t off = (size_t)c0 * p->ntet;
+    b.o_ssd = p->d_ssd + 2 * off;
+    b.o_cov = p->d_cov + 2 * off;
+    b.o_def = p->d_def + off;
+    b.o_fold = p->d_fold + off;
+    launch_setup(p->d_prob, b, p->st);
+    launch_raster(p->d_prob, b, p->storage, p->warps, p->vpw, p->n_sm, p->st);
+    if (p->ng > 0) launch_locate_full(p->d_prob, p->hp, b, c0, nc, p->st);
+    launch_reduce_full(p->d_prob, c0, nc, b, p->d_obj + 4 * (size_t)c0, p->st);
+    CU(cudaGetLastError());
+    // host staging arrays are reused by the next chunk
+    CU(cudaStreamSynchronize(p->st));
+  }
+  bool host_dst;
+  if ((rc = copy_out(obj_out, p->d_obj, sizeof(double) * 4 * n_cand, p->st, host_dst))) return rc;
+  if (host_dst) CU(cudaStreamSynchronize(p->st));
+  return DMR_OK;
+}
+
+int dmr_eval_partial(dmr_problem* p, int n_trials, const int* group_ids, const int* cand_ids,
+                     const double* trial_coords, double* obj_out) {
+  if (!p || !group_ids || !cand_ids || !trial_coords || !obj_out) return fail(DMR_EINVAL, "null argument");
+  if (p->n_groups == 0) return fail(DMR_ESTATE, "no FOS registered");
+  if (p->C == 0) return fail(DMR_ESTATE, "no population (call dmr_eval_full first)");
+  if (n_trials < 1) return fail(DMR_EINVAL, "n_trials must be >= 1");
+  std::vector<int> gid(n_trials), cid(n_trials);
+  CU(cudaMemcpy(gid.data(), group_ids, sizeof(int) * n_trials, cudaMemcpyDefault));
+  CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n_trials, cudaMemcpyDefault));
+  std::vector<int> first(n_trials), ntt(n_trials);
+  long tot = 0;
+  for (int k = 0; k < n_trials; ++k) {
+    if (gid[k] < 0 || gid[k] >= p->n_groups) return fail(DMR_EINVAL, "group id out of range");
+    if (cid[k] < 0 || cid[k] >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+    first[k] = (int)tot;
+    ntt[k] = p->g_tptr[gid[k] + 1] - p->g_tptr[gid[k]];
+    tot += ntt[k];
+  }
+  if (tot > (1L << 30)) return fail(DMR_EINVAL, "too many trial tets");
+  int rc;
+  if ((rc = p->sc.ensure((int)tot, n_trials, p->gmax, 2 * std::max(1, p->ng)))) return rc;
+  std::vector<int> tt_trial(tot), tt_tet(tot);
+  std::vector<uint32_t> tt_slot(tot);
+  for (int k = 0; k < n_trials; ++k) {
+    int g = gid[k];
+    for (int j = 0; j < ntt[k]; ++j) {
+      tt_trial[first[k] + j] = k;
+      tt_tet[first[k] + j] = p->g_tets[p->g_tptr[g] + j];
+      tt_slot[first[k] + j] = p->g_slot[p->g_tptr[g] + j];
+    }
+  }
+  // commit safety: accepted trials of a candidate must touch disjoint tets
+  std::vector<int> order(n_trials);
+  for (int k = 0; k < n_trials; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cid[a] < cid[b]; });
+  std::vector<int> cptr(1, 0), ctr;
+  bool safe = true;
+  {
+    std::vector<int> stamp(p->ntet, -1);
+    int prev = -1, ci = -1;
+    for (int idx : order) {
+      if (cid[idx] != prev) {
+        prev = cid[idx];
+        ++ci;
+        if (ci > 0) cptr.push_back((int)ctr.size());
+      }
+      ctr.push_back(idx);
+      int g = gid[idx];
+      for (int j = p->g_tptr[g]; j < p->g_tptr[g + 1]; ++j) {
+        int t = p->g_tets[j];
+        if (stamp[t] == cid[idx]) safe = false;
+        stamp[t] = cid[idx];
+      }
+    }
+    cptr.push_back((int)ctr.size());
+  }
+  const cudaStream_t st = p->st;
+  CU(cudaMemcpyAsync(p->sc.tt_trial, tt_trial.data(), sizeof(int) * tot, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tt_tet, tt_tet.data(), sizeof(int) * tot, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tt_slot, tt_slot.data(), sizeof(uint32_t) * tot, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_cand, cid.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_group, gid.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_first, first.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_ntt, ntt.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.cand_ptr, cptr.data(), sizeof(int) * cptr.size(), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.cand_trials, ctr.data(), sizeof(int) * ctr.size(), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_coords, trial_coords, sizeof(double) * 6 * p->gmax * (size_t)n_trials, cudaMemcpyDefault,
+                     st));
+  Batch b = make_batch(p, p->sc, (int)tot, n_trials);
+  launch_setup(p->d_prob, b, st);
+  launch_raster(p->d_prob, b, p->storage, p->warps, p->vpw, p->n_sm, st);
+  if (p->ng > 0) launch_landmarks_partial(p->d_prob, b, st);
+  launch_reduce_partial(p->d_prob, b, st);
+  CU(cudaGetLastError());
+  bool host_dst;
+  if ((rc = copy_out(obj_out, p->sc.tr_obj, sizeof(double) * 4 * n_trials, st, host_dst))) return rc;
+  // the host staging vectors die at return: wait for the uploads
+  CU(cudaStreamSynchronize(st));
+  p->have_partial = true;
+  p->partial_safe = safe;
+  p->last_ntr = n_trials;
+  p->last_ntt = (int)tot;
+  p->last_cand = cid;
+  p->last_group = gid;
+  p->last_first = first;
+  p->last_ntt_v = ntt;
+  p->last_nlist = (int)cptr.size() - 1;
+  return DMR_OK;
+}
+
+namespace {
+
+int do_commit(dmr_problem* p, const uint8_t* d_accept) {
+  Batch b = make_batch(p, p->sc, p->last_ntt, p->last_ntr);
+  launch_commit(p->d_prob, b, d_accept, p->sc.tr_group, p->d_gptr, p->d_gpts, p->sc.cand_ptr, p->sc.cand_trials,
+                p->last_nlist, p->st);
+  CU(cudaGetLastError());
+  p->have_partial = false;
+  return DMR_OK;
+}
+
+}  // namespace
+
+int dmr_commit(dmr_problem* p, const uint8_t* accept) {
+  if (!p || !accept) return fail(DMR_EINVAL, "null argument");
+  if (!p->have_partial) return fail(DMR_ESTATE, "no partial evaluation to commit");
+  if (!is_device_ptr(accept)) {
+    // disjointness of accepted trials per candidate
+    std::vector<int> stamp(p->ntet, -1);
+    std::vector<int> order;
+    for (int k = 0; k < p->last_ntr; ++k)
+      if (accept[k]) order.push_back(k);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->last_cand[a] < p->last_cand[b]; });
+    for (int k : order) {
+      int g = p->last_group[k];
+      for (int j = p->g_tptr[g]; j < p->g_tptr[g + 1]; ++j) {
+        int t = p->g_tets[j];
+        if (stamp[t] == p->last_cand[k]) return fail(DMR_EINVAL, "accepted trials of one candidate overlap");
+        stamp[t] = p->last_cand[k];
+      }
+    }
+  }
+  CU(cudaMemcpyAsync(p->sc.accept, accept, p->last_ntr, cudaMemcpyDefault, p->st));
+  int rc = do_commit(p, p->sc.accept);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(p->st));
+  return DMR_OK;
+}
+
+int dmr_commit_improving(dmr_problem* p, uint8_t* accept_out) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (!p->have_partial) return fail(DMR_ESTATE, "no partial evaluation to commit");
+  if (!p->partial_safe) return fail(DMR_EINVAL, "trials of one candidate overlap; commit explicitly");
+  Batch b = make_batch(p, p->sc, p->last_ntt, p->last_ntr);
+  launch_accept(p->d_prob, b, p->sc.accept, p->st);
+  int ntr = p->last_ntr;
+  int rc = do_commit(p, p->sc.accept);
+  if (rc) return rc;
+  if (accept_out) {
+    bool host_dst;
+    if ((rc = copy_out(accept_out, p->sc.accept, ntr, p->st, host_dst))) return rc;
+    if (host_dst) CU(cudaStreamSynchronize(p->st));
+  }
+  return DMR_OK;
+}
+
+int dmr_objectives_out(dmr_problem* p, int n, const int* cand_ids, double* out) {
+  if (!p || !cand_ids || !out) return fail(DMR_EINVAL, "null argument");
+  std::vector<int> cid(std::max(n, 1));
+  CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n, cudaMemcpyDefault));
+  std::vector<double> raw(4 * (size_t)p->cap), res(4 * (size_t)std::max(n, 1));
+  CU(cudaMemcpyAsync(raw.data(), p->d_sums, sizeof(double) * 4 * std::max(p->C, 1), cudaMemcpyDeviceToHost, p->st));
+  CU(cudaStreamSynchronize(p->st));
+  for (int k = 0; k < n; ++k) {
+    if (cid[k] < 0 || cid[k] >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+    const double* s = &raw[4 * (size_t)cid[k]];
+    res[4 * k + 0] = s[0] / p->hp.sim_norm;
+    res[4 * k + 1] = s[1] / p->hp.def_norm;
+    res[4 * k + 2] = p->ng > 0 ? s[2] / p->hp.guid_norm : 0.0;
+    res[4 * k + 3] = s[3];
+  }
+  CU(cudaMemcpy(out, res.data(), sizeof(double) * 4 * n, cudaMemcpyDefault));
+  return DMR_OK;
+}
+
+int dmr_coords_out(dmr_problem* p, int cand, double* out) {
+  if (!p || !out) return fail(DMR_EINVAL, "null argument");
+  if (cand < 0 || cand >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+  CU(cudaStreamSynchronize(p->st));
+  CU(cudaMemcpy(out, p->d_coords + (size_t)cand * 6 * p->P, sizeof(double) * 6 * p->P, cudaMemcpyDefault));
+  return DMR_OK;
+}
+
+int dmr_terms_out(dmr_problem* p, int cand, int* cov, double* ssd, double* def, int* fold) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (cand < 0 || cand >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+  CU(cudaStreamSynchronize(p->st));
+  size_t off = (size_t)cand * p->ntet;
+  if (cov) CU(cudaMemcpy(cov, p->d_cov + 2 * off, sizeof(int) * 2 * p->ntet, cudaMemcpyDefault));
+  if (ssd) CU(cudaMemcpy(ssd, p->d_ssd + 2 * off, sizeof(double) * 2 * p->ntet, cudaMemcpyDefault));
+  if (def) CU(cudaMemcpy(def, p->d_def + off, sizeof(double) * p->ntet, cudaMemcpyDefault));
+  if (fold) CU(cudaMemcpy(fold, p->d_fold + off, sizeof(int) * p->ntet, cudaMemcpyDefault));
+  return DMR_OK;
+}
+
+int dmr_landmarks_out(dmr_problem* p, int cand, int* loc, double* term) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (cand < 0 || cand >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+  if (p->ng == 0) return DMR_OK;
+  CU(cudaStreamSynchronize(p->st));
+  size_t off = (size_t)cand * 2 * p->ng;
+  if (loc) CU(cudaMemcpy(loc, p->d_loc + off, sizeof(int) * 2 * p->ng, cudaMemcpyDefault));
+  if (term) CU(cudaMemcpy(term, p->d_gterm + off, sizeof(double) * 2 * p->ng, cudaMemcpyDefault));
+  return DMR_OK;
+}
+
+int dmr_trial_out(dmr_problem* p, int k, int* tets, int* cov, double* ssd, double* def, int* fold) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (p->last_group.empty()) return fail(DMR_ESTATE, "no partial evaluation");
+  if (k < 0 || k >= p->last_ntr) return fail(DMR_EINVAL, "trial index out of range");
+  CU(cudaStreamSynchronize(p->st));
+  int f = p->last_first[k], n = p->last_ntt_v[k];
+  int g = p->last_group[k];
+  if (tets) memcpy(tets, &p->g_tets[p->g_tptr[g]], sizeof(int) * n);
+  if (cov) CU(cudaMemcpy(cov, p->sc.o_cov + 2 * (size_t)f, sizeof(int) * 2 * n, cudaMemcpyDefault));
+  if (ssd) CU(cudaMemcpy(ssd, p->sc.o_ssd + 2 * (size_t)f, sizeof(double) * 2 * n, cudaMemcpyDefault));
+  if (def) CU(cudaMemcpy(def, p->sc.o_def + f, sizeof(double) * n, cudaMemcpyDefault));
+  if (fold) CU(cudaMemcpy(fold, p->sc.o_fold + f, sizeof(int) * n, cudaMemcpyDefault));
+  return n;
+}
+
+int dmr_samples(dmr_problem* p, long long* samples, int reset) {
+  if (!p || !samples) return fail(DMR_EINVAL, "null argument");
+  unsigned long long v = 0;
+  CU(cudaMemcpyAsync(&v, p->d_samples, sizeof(v), cudaMemcpyDeviceToHost, p->st));
+  CU(cudaStreamSynchronize(p->st));
+  *samples = (long long)v;
+  if (reset) CU(cudaMemsetAsync(p->d_samples, 0, sizeof(v), p->st));
+  return DMR_OK;
+}
+
+// ------------------------------------------------------------ generation plan
+int dmr_plan_destroy(dmr_plan* pl) {
+  if (!pl) return DMR_OK;
+  if (pl->p) cudaStreamSynchronize(pl->p->st);
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  dfree(pl->tt_trial); dfree(pl->tt_tet); dfree(pl->tt_slot); dfree(pl->tr_cand); dfree(pl->tr_first);
+  dfree(pl->tr_ntt); dfree(pl->tr_group); dfree(pl->deltas); dfree(pl->cand_ptr); dfree(pl->cand_trials);
+  pl->sc.release();
+  delete pl;
+  return DMR_OK;
+}
+
+int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const double* deltas, dmr_plan** out) {
+  if (!p || !cand_ids || !deltas || !out) return fail(DMR_EINVAL, "null argument");
+  *out = nullptr;
+  if (p->n_groups == 0) return fail(DMR_ESTATE, "no FOS registered");
+  if (p->C == 0) return fail(DMR_ESTATE, "no population (call dmr_eval_full first)");
+  if (n_cand < 1 || n_cand > p->C) return fail(DMR_EINVAL, "n_cand out of range");
+  std::vector<int> cid(n_cand);
+  CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n_cand, cudaMemcpyDefault));
+  {
+    std::vector<int> s(cid);
+    std::sort(s.begin(), s.end());
+    for (int k = 0; k < n_cand; ++k) {
+      if (s[k] < 0 || s[k] >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+      if (k && s[k] == s[k - 1]) return fail(DMR_EINVAL, "duplicate candidate id");
+    }
+  }
+  const int G = p->gmax;
+  const int nw = (int)p->wave_ptr.size() - 1;
+  size_t dl_per = (size_t)6 * G;
+  std::vector<double> hd((size_t)p->n_groups * n_cand * dl_per);
+  CU(cudaMemcpy(hd.data(), deltas, sizeof(double) * hd.size(), cudaMemcpyDefault));
+  dmr_plan* pl = new (std::nothrow) dmr_plan();
+  if (!pl) return fail(DMR_ENOMEM, "host allocation failed");
+  pl->p = p;
+  // arrays for all waves: trials ordered (wave, candidate, group)
+  std::vector<int> tt_trial, tt_tet, tr_cand, tr_first, tr_ntt, tr_group, cptr, ctr;
+  std::vector<uint32_t> tt_slot;
+  std::vector<double> dl;
+  std::vector<int> w_tt0, w_ntt, w_tr0, w_ntr, w_c0;
+  int max_tt = 0, max_tr = 0;
+  for (int w = 0; w < nw; ++w) {
+    w_tt0.push_back((int)tt_trial.size());
+    w_tr0.push_back((int)tr_cand.size());
+    w_c0.push_back((int)cptr.size());
+    int k = 0, ttw = 0;
+    for (int ci = 0; ci < n_cand; ++ci) {
+      cptr.push_back(k);
+      for (int gi = p->wave_ptr[w]; gi < p->wave_ptr[w + 1]; ++gi, ++k) {
+        int g = p->wave_groups[gi];
+        ctr.push_back(k);
+        tr_cand.push_back(cid[ci]);
+        tr_group.push_back(g);
+        tr_first.push_back(ttw);
+        int n = p->g_tptr[g + 1] - p->g_tptr[g];
+        tr_ntt.push_back(n);
+        for (int j = 0; j < n; ++j) {
+          tt_trial.push_back(k);
+          tt_tet.push_back(p->g_tets[p->g_tptr[g] + j]);
+          tt_slot.push_back(p->g_slot[p->g_tptr[g] + j]);
+        }
+        ttw += n;
+        const double* src = &hd[((size_t)g * n_cand + ci) * dl_per];
+        dl.insert(dl.end(), src, src + dl_per);
+      }
+    }
+    cptr.push_back(k);
+    w_ntt.push_back(ttw);
+    w_ntr.push_back(k);
+    max_tt = std::max(max_tt, ttw);
+    max_tr = std::max(max_tr, k);
+  }
+  int rc;
+  if ((rc = dalloc(&pl->tt_trial, tt_trial.size())) || (rc = dalloc(&pl->tt_tet, tt_tet.size())) ||
+      (rc = dalloc(&pl->tt_slot, tt_slot.size())) || (rc = dalloc(&pl->tr_cand, tr_cand.size())) ||
+      (rc = dalloc(&pl->tr_first, tr_first.size())) || (rc = dalloc(&pl->tr_ntt, tr_ntt.size())) ||
+      (rc = dalloc(&pl->tr_group, tr_group.size())) || (rc = dalloc(&pl->deltas, dl.size())) ||
+      (rc = dalloc(&pl->cand_ptr, cptr.size())) || (rc = dalloc(&pl->cand_trials, ctr.size())) ||
+      (rc = pl->sc.ensure(max_tt, max_tr, G, 2 * std::max(1, p->ng)))) {
+    dmr_plan_destroy(pl);
+    return rc;
+  }
+  auto up = [&](void* d, const void* h, size_t bytes) { return cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice); };
+  if (up(pl->tt_trial, tt_trial.data(), 4 * tt_trial.size()) || up(pl->tt_tet, tt_tet.data(), 4 * tt_tet.size()) ||
+      up(pl->tt_slot, tt_slot.data(), 4 * tt_slot.size()) || up(pl->tr_cand, tr_cand.data(), 4 * tr_cand.size()) ||
+      up(pl->tr_first, tr_first.data(), 4 * tr_first.size()) || up(pl->tr_ntt, tr_ntt.data(), 4 * tr_ntt.size()) ||
+      up(pl->tr_group, tr_group.data(), 4 * tr_group.size()) || up(pl->deltas, dl.data(), 8 * dl.size()) ||
+      up(pl->cand_ptr, cptr.data(), 4 * cptr.size()) || up(pl->cand_trials, ctr.data(), 4 * ctr.size())) {
+    dmr_plan_destroy(pl);
+    return fail(DMR_ECUDA, "plan upload failed");
+  }
+  // capture all waves into one graph
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    dmr_plan_destroy(pl);
+    return fail(DMR_ECUDA, "stream create failed");
+  }
+  cudaStreamSynchronize(p->st);
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int launches = 0;
+  for (int w = 0; w < nw && e == cudaSuccess; ++w) {
+    Batch b = make_batch(p, pl->sc, w_ntt[w], w_ntr[w]);
+    b.tt_trial = pl->tt_trial + w_tt0[w];
+    b.tt_tet = pl->tt_tet + w_tt0[w];
+    b.tt_slot = pl->tt_slot + w_tt0[w];
+    b.tr_cand = pl->tr_cand + w_tr0[w];
+    b.tr_first = pl->tr_first + w_tr0[w];
+    b.tr_ntt = pl->tr_ntt + w_tr0[w];
+    b.gmax = G;
+    const int* trg = pl->tr_group + w_tr0[w];
+    launch_propose(p->d_prob, b, trg, p->d_gptr, p->d_gpts, pl->deltas + (size_t)w_tr0[w] * dl_per, cs);
+    launch_setup(p->d_prob, b, cs);
+    launch_raster(p->d_prob, b, p->storage, p->warps, p->vpw, p->n_sm, cs);
+    launches += 3;
+    if (p->ng > 0) {
+      launch_landmarks_partial(p->d_prob, b, cs);
+      ++launches;
+    }
+    launch_reduce_partial(p->d_prob, b, cs);
+    launch_accept(p->d_prob, b, pl->sc.accept, cs);
+    launch_commit(p->d_prob, b, pl->sc.accept, trg, p->d_gptr, p->d_gpts, pl->cand_ptr + w_c0[w],
+                  pl->cand_trials + w_tr0[w], n_cand, cs);
+    launches += 5;
+    e = cudaGetLastError();
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    dmr_plan_destroy(pl);
+    return fail(DMR_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  pl->graph = g;
+  e = cudaGraphInstantiate(&pl->exec, g, 0);
+  if (e != cudaSuccess) {
+    dmr_plan_destroy(pl);
+    return fail(DMR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  pl->launches = launches;
+  p->have_partial = false;
+  *out = pl;
+  return DMR_OK;
+}
+
+int dmr_plan_run(dmr_plan* pl) {
+  if (!pl || !pl->exec) return fail(DMR_EINVAL, "null plan");
+  CU(cudaGraphLaunch(pl->exec, pl->p->st));
+  return DMR_OK;
+}
+
+int dmr_plan_launches(const dmr_plan* pl, int* launches) {
+  if (!pl || !launches) return fail(DMR_EINVAL, "null argument");
+  *launches = pl->launches;
+  return DMR_OK;
+}
+
+}  // extern "C"

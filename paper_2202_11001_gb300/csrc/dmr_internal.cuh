@@ -1,0 +1,127 @@
+// Internal structures shared by the host API (dmr_api.cu) and the kernels
+// (dmr_kernels.cu) of the GB300 dual simplex-mesh evaluator.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dmr {
+
+// Image storage types (match DMR_F32 / DMR_BF16 / DMR_F16 of dmr.h).
+enum { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
+
+// Everything a kernel needs to know about one registration problem.  Lives
+// in device memory (an array of these for batched launches).
+struct DevProblem {
+  // images: plain [nz][ny][nx] and corner-packed cells
+  // [(nz+2)][(ny+2)][(nx+2)] x 8 corners for cell origins -1..n per axis
+  // (corner values pre-clamped to the image), plus per-cell zero flags
+  // (bit0: some corner is 0, bit1: all corners are 0).
+  const void* plain[2];
+  const void* cells[2];
+  const uint8_t* cflag[2];
+  int n[2][3];
+  double spd[2][3];
+  float sp[2][3];
+  int dtype;
+  // topology
+  int P, ntet;
+  int m[3];
+  const int4* tet;          // [ntet] point ids, positive rest orientation
+  const uint32_t* fperm;    // [ntet] 4 faces x 8 bits: a|b<<2|c<<4|neg<<6
+  const uint8_t* fixmask;   // [P] bit a: axis a fixed; bit 3+a: upper border
+  const float* rest_vol;    // [ntet] source rest volume (mm^3), LINEAR model
+  int black_rule, model;
+  float lam, mu;
+  double sim_norm, def_norm, guid_norm;
+  int ng;
+  const double* guide;      // [ng][2][3]
+  // population state
+  int C;
+  double* coords;           // [C][2][3][P]
+  double* c_ssd;            // [C][ntet][2]
+  int* c_cov;               // [C][ntet][2]
+  double* c_def;            // [C][ntet]
+  int* c_fold;              // [C][ntet]
+  int* c_loc;               // [C][2][ng]
+  double* c_gterm;          // [C][2][ng]
+  double* sums;             // [C][4] raw sums
+  unsigned long long* samples;
+};
+
+// Per (trial, tet, direction) set-up produced by the geometry kernel and
+// consumed by the rasterise-and-sample kernel and the landmark kernels.
+// "own" = the mesh whose voxels are visited (direction 0: source, 1: target),
+// "partner" = the other mesh.  Relative coordinates are taken against the
+// integer origins O (own) and Op (partner).
+struct __align__(16) ItemRec {
+  int flags;        // bit0: rasterise (6V_own > 0)
+  int prob;
+  int tet;
+  int dir;
+  int b0[4];        // clipped integer bbox, abs voxel coords (x,y,z,-)
+  int b1[4];
+  int O[4];         // own origin (floor of min vertex coords)
+  int Op[4];        // partner origin
+  unsigned cbase;   // corner-cell index offset (mod 2^32, see kernels)
+  int pad0[3];
+  float vr[4][4];   // own vertices relative to O (x,y,z,-)
+  float fa[4][4];   // face f: inward normal A (x,y,z), offset B'
+  float fm[4][4];   // face f: margin mu, 1/A.x, -, -
+  float G[3][4];    // map matrix rows (FP32), col 3 = k (offset)
+  float gx[4];      // (1+G00, G10, G20, delta)
+  float clo[4];     // clamp range of partner-relative mapped coords
+  float chi[4];
+  double X[4][3];   // own vertices FP64 (abs)
+  double G64[3][3]; // FP64 map matrix
+  double d0[3];     // partner_0 - own_0
+};
+
+// A batch of (trial, tet) pairs to evaluate.
+struct Batch {
+  int n_tt;
+  const int* tt_trial;      // [n_tt]
+  const int* tt_tet;        // [n_tt] ascending within a trial
+  const uint32_t* tt_slot;  // [n_tt] 4 x 8 bit: (group slot + 1) of vertex i, 0 = unmoved; NULL = none
+  int n_trials;
+  const int* tr_prob;       // [n_trials] or NULL (problem 0)
+  const int* tr_cand;       // [n_trials]
+  const int* tr_first;      // [n_trials] first tt index
+  const int* tr_ntt;        // [n_trials]
+  const double* tr_coords;  // [n_trials][2][3][gmax] or NULL (full evaluation)
+  int gmax;
+  ItemRec* rec;             // [2 n_tt]
+  double* o_ssd;            // [n_tt][2]
+  int* o_cov;               // [n_tt][2]
+  double* o_def;            // [n_tt]
+  int* o_fold;              // [n_tt]
+  unsigned* work;           // raster work counter
+  // partial-evaluation landmark outputs
+  int aff_cap;
+  int* aff_n;               // [n_trials]
+  int* aff_idx;             // [n_trials][aff_cap]  mesh*ng + i
+  int* aff_loc;             // [n_trials][aff_cap]
+  double* aff_term;         // [n_trials][aff_cap]
+  double* tr_delta;         // [n_trials][4]
+  double* tr_obj;           // [n_trials][4]
+};
+
+// Kernel launchers (dmr_kernels.cu).  All enqueue on `st`.
+void launch_convert_image(const void* src, int src_dtype, void* dst, int dst_dtype, long n, cudaStream_t st);
+void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag, cudaStream_t st);
+void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
+void launch_raster(const DevProblem* probs, const Batch& b, int storage_dtype, int warps, int vpw, int n_sm,
+                   cudaStream_t st);
+void launch_locate_full(const DevProblem* probs, const DevProblem& host_pr, const Batch& b, int c0, int nc,
+                        cudaStream_t st);
+void launch_reduce_full(const DevProblem* probs, int c0, int nc, const Batch& b, double* obj, cudaStream_t st);
+void launch_landmarks_partial(const DevProblem* probs, const Batch& b, cudaStream_t st);
+void launch_reduce_partial(const DevProblem* probs, const Batch& b, cudaStream_t st);
+void launch_accept(const DevProblem* probs, const Batch& b, uint8_t* accept, cudaStream_t st);
+void launch_commit(const DevProblem* probs, const Batch& b, const uint8_t* accept, const int* tr_group,
+                   const int* g_ptr, const int* g_pts, const int* cand_ptr, const int* cand_trials, int n_list,
+                   cudaStream_t st);
+void launch_propose(const DevProblem* probs, const Batch& b, const int* tr_group, const int* g_ptr, const int* g_pts,
+                    const double* deltas, cudaStream_t st);
+
+}  // namespace dmr

@@ -1,0 +1,365 @@
+"""Thin Python binding of the C-ABI in ``include/dmr.h`` (libdmr.so).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  Arrays may be numpy arrays (host) or torch tensors (host or
+device); device tensors are passed by pointer without copies.  There is no
+CPU fallback: if the CUDA library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdmr.so")
+
+F32, BF16, F16 = 0, 1, 2
+SPRING, LINEAR = 0, 1
+_DT = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16, "f16": F16, "float16": F16}
+
+_lib = None
+
+
+class DmrError(RuntimeError):
+    pass
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("img", ctypes.c_void_p * 2),
+        ("img_dtype", ctypes.c_int),
+        ("dims", (ctypes.c_int * 3) * 2),
+        ("spacing", (ctypes.c_double * 3) * 2),
+        ("storage_dtype", ctypes.c_int),
+        ("mesh_pts", ctypes.c_int * 3),
+        ("guide", ctypes.c_void_p),
+        ("n_guide", ctypes.c_int),
+        ("black_rule", ctypes.c_int),
+        ("deform_model", ctypes.c_int),
+        ("lam", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("max_candidates", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+def load():
+    """Load libdmr.so (built in-tree by ``build.build_library``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise DmrError("CUDA library %s is not built; run __graft_entry__.build()" % LIB_PATH)
+    try:  # share one CUDA runtime with torch when it is present
+        import torch  # noqa: F401
+    except ImportError:
+        pass
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, ip = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+    sig = {
+        "dmr_problem_create": [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)],
+        "dmr_problem_destroy": [vp],
+        "dmr_set_stream": [vp, vp],
+        "dmr_problem_info": [vp, ip, ip],
+        "dmr_tets_out": [vp, ip],
+        "dmr_set_fos": [vp, i, ip, ip],
+        "dmr_fos_info": [vp, ip, ip, ip],
+        "dmr_fos_waves": [vp, ip, ip],
+        "dmr_eval_full": [vp, i, vp, vp],
+        "dmr_eval_partial": [vp, i, vp, vp, vp, vp],
+        "dmr_commit": [vp, vp],
+        "dmr_commit_improving": [vp, vp],
+        "dmr_objectives_out": [vp, i, vp, vp],
+        "dmr_coords_out": [vp, i, vp],
+        "dmr_terms_out": [vp, i, vp, vp, vp, vp],
+        "dmr_landmarks_out": [vp, i, vp, vp],
+        "dmr_trial_out": [vp, i, vp, vp, vp, vp, vp],
+        "dmr_samples": [vp, ctypes.POINTER(ctypes.c_longlong), i],
+        "dmr_plan_generation": [vp, i, vp, vp, ctypes.POINTER(ctypes.c_void_p)],
+        "dmr_plan_run": [vp],
+        "dmr_plan_destroy": [vp],
+        "dmr_plan_launches": [vp, ip],
+        "dmr_set_tile": [vp, i, i],
+        "dmr_get_tile": [vp, ip, ip],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.dmr_last_error.restype = ctypes.c_char_p
+    lib.dmr_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return [
+        "dmr_problem_create", "dmr_problem_destroy", "dmr_set_stream", "dmr_problem_info", "dmr_tets_out",
+        "dmr_set_fos", "dmr_fos_info", "dmr_fos_waves", "dmr_eval_full", "dmr_eval_partial", "dmr_commit",
+        "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
+        "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
+        "dmr_plan_launches", "dmr_set_tile", "dmr_get_tile", "dmr_last_error",
+    ]
+
+
+def _check(rc):
+    if rc < 0:
+        raise DmrError("dmr error %d: %s" % (rc, _lib.dmr_last_error().decode()))
+    return rc
+
+
+class _Arg:
+    """Pointer to an array argument: numpy (host) or torch (host/device)."""
+
+    def __init__(self, a, dtype):
+        self.keep = None
+        if a is None:
+            self.ptr = None
+            return
+        try:
+            import torch
+
+            if isinstance(a, torch.Tensor):
+                want = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8,
+                        np.float32: torch.float32, np.uint16: torch.int16}[dtype]
+                t = a.contiguous()
+                if t.dtype != want and not (dtype == np.uint16 and t.dtype in (torch.bfloat16, torch.float16)):
+                    t = t.to(want)
+                self.keep = t
+                self.ptr = t.data_ptr()
+                return
+        except ImportError:
+            pass
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        self.keep = arr
+        self.ptr = arr.ctypes.data
+
+
+def _ptr(a, dtype):
+    return _Arg(a, dtype)
+
+
+def _is_torch(a):
+    try:
+        import torch
+
+        return isinstance(a, torch.Tensor)
+    except ImportError:
+        return False
+
+
+def _out_like(ref, shape, dtype):
+    """Output buffer on the same device as ``ref`` (torch) or numpy."""
+    if _is_torch(ref):
+        import torch
+
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.zeros(shape, dtype)
+
+
+def _addr(buf):
+    return buf.data_ptr() if _is_torch(buf) else buf.ctypes.data
+
+
+class Problem:
+    """One registration problem plus its candidate population (C-ABI handle)."""
+
+    def __init__(self, img_s, img_t, spacing_s, spacing_t, mesh_pts, guide=None, black_rule=True,
+                 model=SPRING, lam=1.0, mu=1.0, storage="f32", max_candidates=1, stream=None,
+                 img_dtype=None):
+        lib = load()
+        self._lib = lib
+        d = _Desc()
+        imgs = [img_s, img_t]
+        if img_dtype is None:
+            img_dtype = "f32"
+        idt = _DT[img_dtype] if isinstance(img_dtype, str) else int(img_dtype)
+        self._keep = []
+        for k, im in enumerate(imgs):
+            if _is_torch(im):
+                shape = tuple(im.shape)
+                a = _Arg(im, np.float32 if idt == F32 else np.uint16)
+            else:
+                shape = np.asarray(im).shape
+                a = _Arg(im, np.float32 if idt == F32 else np.uint16)
+            self._keep.append(a)
+            d.img[k] = a.ptr
+            nz, ny, nx = shape
+            d.dims[k][0], d.dims[k][1], d.dims[k][2] = nx, ny, nz
+        sps = [spacing_s, spacing_t]
+        for k in range(2):
+            for a in range(3):
+                d.spacing[k][a] = float(sps[k][a])
+        d.img_dtype = idt
+        d.storage_dtype = _DT[storage] if isinstance(storage, str) else int(storage)
+        for a in range(3):
+            d.mesh_pts[a] = int(mesh_pts[a])
+        self.ng = 0
+        if guide is not None and len(guide):
+            g = np.ascontiguousarray(np.asarray(guide, np.float64).reshape(-1, 2, 3))
+            self._guide = g
+            d.guide = g.ctypes.data
+            d.n_guide = g.shape[0]
+            self.ng = g.shape[0]
+        d.black_rule = int(bool(black_rule))
+        d.deform_model = int(model)
+        d.lam = float(lam)
+        d.mu = float(mu)
+        d.max_candidates = int(max_candidates)
+        d.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.dmr_problem_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        self._keep = None
+        P, T = ctypes.c_int(), ctypes.c_int()
+        lib.dmr_problem_info(self.h, ctypes.byref(P), ctypes.byref(T))
+        self.P, self.ntet = P.value, T.value
+        self.C = 0
+        self.gmax = 0
+        self._groups = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dmr_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(self._lib.dmr_set_stream(self.h, stream))
+
+    def tets(self):
+        out = np.zeros((self.ntet, 4), np.int32)
+        _check(self._lib.dmr_tets_out(self.h, out.ctypes.data))
+        return out
+
+    def set_tile(self, warps=0, voxels_per_warp=0):
+        _check(self._lib.dmr_set_tile(self.h, int(warps), int(voxels_per_warp)))
+
+    # -- FOS --------------------------------------------------------------
+    def set_fos(self, groups):
+        ptr = np.zeros(len(groups) + 1, np.int32)
+        for g, pts in enumerate(groups):
+            ptr[g + 1] = ptr[g] + len(pts)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int32) for x in groups]))
+        _check(self._lib.dmr_set_fos(self.h, len(groups), ptr.ctypes.data, flat.ctypes.data))
+        mg, mt, nw = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.dmr_fos_info(self.h, ctypes.byref(mg), ctypes.byref(mt), ctypes.byref(nw)))
+        self.gmax, self.max_touched, self.n_waves = mg.value, mt.value, nw.value
+        self._groups = [np.asarray(x, np.int32) for x in groups]
+
+    def waves(self):
+        wp = np.zeros(self.n_waves + 1, np.int32)
+        wg = np.zeros(len(self._groups), np.int32)
+        _check(self._lib.dmr_fos_waves(self.h, wp.ctypes.data, wg.ctypes.data))
+        return [wg[wp[w]:wp[w + 1]] for w in range(self.n_waves)]
+
+    # -- evaluation -------------------------------------------------------
+    def eval_full(self, coords, out=None):
+        C = coords.shape[0]
+        a = _Arg(coords, np.float64)
+        obj = out if out is not None else _out_like(coords, (C, 4), np.float64)
+        _check(self._lib.dmr_eval_full(self.h, C, a.ptr, _addr(obj)))
+        self.C = C
+        return obj
+
+    def eval_partial(self, group_ids, cand_ids, trial_coords, out=None):
+        n = len(group_ids)
+        g = _Arg(group_ids, np.int32)
+        c = _Arg(cand_ids, np.int32)
+        tc = _Arg(trial_coords, np.float64)
+        obj = out if out is not None else _out_like(trial_coords, (n, 4), np.float64)
+        _check(self._lib.dmr_eval_partial(self.h, n, g.ptr, c.ptr, tc.ptr, _addr(obj)))
+        self._ntr = n
+        return obj
+
+    def commit(self, accept):
+        a = _Arg(accept, np.uint8)
+        _check(self._lib.dmr_commit(self.h, a.ptr))
+
+    def commit_improving(self, want_accept=True):
+        out = np.zeros(self._ntr, np.uint8) if want_accept else None
+        _check(self._lib.dmr_commit_improving(self.h, out.ctypes.data if out is not None else None))
+        return out
+
+    def objectives(self, cands=None):
+        cands = np.arange(self.C, dtype=np.int32) if cands is None else np.asarray(cands, np.int32)
+        out = np.zeros((len(cands), 4), np.float64)
+        _check(self._lib.dmr_objectives_out(self.h, len(cands), cands.ctypes.data, out.ctypes.data))
+        return out
+
+    def coords(self, c):
+        out = np.zeros((2, 3, self.P), np.float64)
+        _check(self._lib.dmr_coords_out(self.h, int(c), out.ctypes.data))
+        return out
+
+    def terms(self, c):
+        cov = np.zeros((self.ntet, 2), np.int32)
+        ssd = np.zeros((self.ntet, 2), np.float64)
+        de = np.zeros(self.ntet, np.float64)
+        fo = np.zeros(self.ntet, np.int32)
+        _check(self._lib.dmr_terms_out(self.h, int(c), cov.ctypes.data, ssd.ctypes.data, de.ctypes.data,
+                                       fo.ctypes.data))
+        return {"cov": cov, "ssd": ssd, "def": de, "fold": fo}
+
+    def landmarks(self, c):
+        n = max(self.ng, 1)
+        loc = np.zeros((2, n), np.int32)
+        gt = np.zeros((2, n), np.float64)
+        _check(self._lib.dmr_landmarks_out(self.h, int(c), loc.ctypes.data, gt.ctypes.data))
+        return loc[:, : self.ng], gt[:, : self.ng]
+
+    def trial(self, k, cap=None):
+        cap = cap or max(self.max_touched, 1)
+        tets = np.zeros(cap, np.int32)
+        cov = np.zeros((cap, 2), np.int32)
+        ssd = np.zeros((cap, 2), np.float64)
+        de = np.zeros(cap, np.float64)
+        fo = np.zeros(cap, np.int32)
+        n = _check(self._lib.dmr_trial_out(self.h, int(k), tets.ctypes.data, cov.ctypes.data, ssd.ctypes.data,
+                                           de.ctypes.data, fo.ctypes.data))
+        return {"tets": tets[:n], "cov": cov[:n], "ssd": ssd[:n], "def": de[:n], "fold": fo[:n]}
+
+    def samples(self, reset=False):
+        v = ctypes.c_longlong()
+        _check(self._lib.dmr_samples(self.h, ctypes.byref(v), int(bool(reset))))
+        return v.value
+
+    def plan_generation(self, cand_ids, deltas):
+        c = _Arg(cand_ids, np.int32)
+        d = _Arg(deltas, np.float64)
+        h = ctypes.c_void_p()
+        _check(self._lib.dmr_plan_generation(self.h, len(cand_ids), c.ptr, d.ptr, ctypes.byref(h)))
+        return Plan(self, h)
+
+
+class Plan:
+    """A CUDA graph running one GOMEA generation of partial evaluations."""
+
+    def __init__(self, prob, h):
+        self.prob = prob
+        self.h = h
+        n = ctypes.c_int()
+        _check(prob._lib.dmr_plan_launches(self.h, ctypes.byref(n)))
+        self.launches = n.value
+
+    def run(self):
+        _check(self.prob._lib.dmr_plan_run(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.prob._lib.dmr_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
