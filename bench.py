@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark: voxel-samples/s of batched partial objective evaluation.
+
+One step = one GOMEA generation of partial evaluations (Sec. 2.2) of the
+dual simplex-mesh registration objectives (Sec. 2.3) over the whole
+population: for every wave of independent FOS groups, propose, evaluate the
+touched tetrahedra of every (group, candidate) trial, accept-if-improves and
+commit -- one CUDA-graph launch.  One voxel-sample is one (candidate,
+direction, voxel) squared-difference term.
+
+Default workload: 64^3 float32 ellipsoid pair, 5^3-point meshes (384 tets),
+20 guidance pairs, population 128, 125 single-point FOS groups.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (its own
+population; there is no data-path exchange) and rank 0 prints one JSON line
+with the whole-job throughput.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-samples/s of batched partial objective eval"
+UNIT = "voxel-samples/s"
+# Minimal FP32 lane operations one voxel-sample needs by definition (affine
+# map 9, floor/fraction 6, cell index 2, trilinear 7 lerps = 14, difference
+# and square 2, black test 3, accumulate 1).
+ALG_OPS_PER_SAMPLE = 37
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload(name, seed):
+    from paper_2202_11001_gb300 import synth
+
+    if name == "ellipsoid64":
+        pr = synth.ellipsoid_pair(seed=1 + seed, C=128)
+        pr["sigma"] = 1.5
+        pr["desc"] = ("ellipsoid64: 64^3 float32 pair (3 ellipsoids 0.3/0.6/1.0 on 0, target warped by 4 "
+                      "Gaussian bumps <= 6 vox), 5^3-point meshes (384 tets), 20 guidance pairs, population 128, "
+                      "one generation over 125 single-point FOS groups")
+    elif name == "ct":
+        pr = synth.ct_phantom(seed=3 + seed, C=512)
+        pr["sigma"] = 2.0
+        pr["desc"] = ("ct256: 256x256x96 CT phantom mapped to [0,1], spacing 1x1x3 mm, 10^3-point meshes "
+                      "(4374 tets), 200 guidance pairs, population 512, one generation over 1000 single-point groups")
+    elif name == "ct_coarse":
+        pr = synth.ct_phantom(seed=3 + seed, C=512, level="coarse")
+        pr["sigma"] = 0.5
+        pr["desc"] = "ct64 coarse level: 64x64x24, spacing 4x4x12 mm, 10^3-point meshes, population 512"
+    elif name == "sphere16":
+        pr = synth.sphere_pair(seed=seed, C=10)
+        pr["sigma"] = 0.4
+        pr["desc"] = "sphere16: 16^3 float32 pair, 3^3-point meshes (48 tets), 5 guidance pairs, population 10"
+    else:
+        raise SystemExit("unknown workload " + name)
+    return pr
+
+
+def deltas_for(pr, groups, C, rng):
+    from paper_2202_11001_gb300 import synth
+
+    fix = synth.fixed_axes(pr["mesh"])
+    d = rng.normal(0.0, pr["sigma"], size=(len(groups), C, 2, 3, 1))
+    for gi, grp in enumerate(groups):
+        for ax in range(3):
+            if (fix[grp[0]] >> ax) & 1:
+                d[gi, :, :, ax, 0] = 0.0
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception as e:  # pragma: no cover
+            log("clock sampling unavailable:", e)
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def cpu_baseline(pr, groups, waves, C, rng_seed, budget_s=20.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample:
+    partial evaluations of the first waves of the generation."""
+    from oracle import oracle as orc
+    from paper_2202_11001_gb300 import synth
+
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    src, tgt = pr["img"]
+    o = orc.Oracle(src, tgt, *pr["spacing"], pr["mesh"], guide=pr["guide"], model=orc.LINEAR)
+    o.eval_full(pr["coords"])
+    rng = np.random.default_rng(rng_seed)
+    samples, secs, nw, ntr = 0, 0.0, 0, 0
+    for w in waves:
+        gids = np.repeat(w, C)
+        cids = np.tile(np.arange(C), len(w))
+        cur = np.stack([o.coords(c) for c in range(C)])
+        tc = synth.trial_coords(cur, groups, gids, cids, pr["sigma"], pr["mesh"], rng)
+        t0 = time.perf_counter()
+        o.eval_partial(groups, gids, cids, tc)
+        secs += time.perf_counter() - t0
+        for k in range(len(gids)):
+            samples += int(o.trial(k, cap=256)["cov"].sum())
+        nw += 1
+        ntr += len(gids)
+        if secs >= budget_s:
+            break
+    return {"value": samples / secs, "unit": UNIT, "cores": orc.max_threads() if cores > 1 else 1,
+            "kind": "oracle", "sample": "%d of %d waves (%d trials, %d voxel-samples), FP64 C oracle, OpenMP over "
+                                         "trials, %.1f s" % (nw, len(waves), ntr, samples, secs)}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle, timed on the host cores, on bounded
+    samples of the same workload (one wave of the generation per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    from paper_2202_11001_gb300 import synth
+
+    pr = workload(args.workload, 0)
+    C = pr["coords"].shape[0]
+    groups = synth.single_point_fos(pr["mesh"])
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    src, tgt = pr["img"]
+    o = orc.Oracle(src, tgt, *pr["spacing"], pr["mesh"], guide=pr["guide"], model=orc.LINEAR)
+    o.eval_full(pr["coords"])
+    # waves of independent groups: points with equal coordinate parity
+    m = pr["mesh"]
+    par = [((p % m[0]) & 1) + 2 * (((p // m[0]) % m[1]) & 1) + 4 * ((p // (m[0] * m[1])) & 1) for p in range(len(groups))]
+    waves = [np.array([g for g in range(len(groups)) if par[g] == c]) for c in range(8)]
+    ncand = max(8, C // 4)
+    rng = np.random.default_rng(11)
+    tot_s, tot_n = 0.0, 0
+    for step in range(args.warmup + args.steps):
+        w = waves[step % 8]
+        gids = np.repeat(w, ncand)
+        cids = np.tile(np.arange(ncand), len(w))
+        cur = np.stack([o.coords(c) for c in range(ncand)])
+        tc = synth.trial_coords(cur, groups, gids, cids, pr["sigma"], pr["mesh"], rng)
+        t0 = time.perf_counter()
+        o.eval_partial(groups, gids, cids, tc)
+        dt = time.perf_counter() - t0
+        n = sum(int(o.trial(k, cap=256)["cov"].sum()) for k in range(len(gids)))
+        if step >= args.warmup:
+            tot_s += dt
+            tot_n += n
+    value = tot_n / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": pr["desc"], "step": "one wave of partial evaluations for "
+                                                                     "%d candidates (bounded sample)" % ncand},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": orc.max_threads(),
+                             "sample": "one wave x %d candidates per step" % ncand},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ellipsoid64")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warm-up raised to 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2202_11001_gb300 import dmr, synth
+
+    pr = workload(args.workload, rank)
+    C = pr["coords"].shape[0]
+    src, tgt = pr["img"]
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def build(storage):
+        g = dmr.Problem(src, tgt, *pr["spacing"], pr["mesh"], guide=pr["guide"], model=dmr.LINEAR,
+                        storage=storage, max_candidates=C, stream=stream)
+        g.eval_full(torch.from_numpy(pr["coords"]).cuda())
+        groups = synth.single_point_fos(pr["mesh"])
+        g.set_fos(groups)
+        return g, groups
+
+    g, groups = build(args.storage)
+    waves = g.waves()
+    rng = np.random.default_rng(100 + rank)
+    deltas = deltas_for(pr, groups, C, rng)
+    plan = g.plan_generation(np.arange(C, dtype=np.int32), deltas)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        plan.run()
+    torch.cuda.synchronize()
+    g.samples(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, raster_ms, setup_ms = [], 0.0, 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed step
+        ev0.record()
+        plan.run()
+        ev1.record()
+        torch.cuda.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        su, ra = plan.kernel_ms()
+        setup_ms += su
+        raster_ms += ra
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    samples = g.samples(reset=True)
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s, float(samples)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        total_s, all_samples = float(tmax[0]), float(t[1])
+    else:
+        all_samples = float(samples)
+    value = all_samples / total_s
+    samples_per_step = samples / args.steps
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+
+    # e2e: the public API with host (pinned) buffers, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        cur0 = pr["coords"]
+        per_wave = []
+        h2d = d2h = 0
+        for w in waves:
+            cids = np.repeat(np.arange(C), len(w)).astype(np.int32)
+            gids = np.tile(w, C).astype(np.int32)
+            tc = np.stack([cur0[c][:, :, groups[gg]] + deltas[gg, c] for gg, c in zip(gids, cids)])
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            per_wave.append((pin(gids), pin(cids), pin(tc), torch.empty((len(gids), 4), dtype=torch.float64,
+                                                                        pin_memory=True)))
+            h2d += gids.nbytes + cids.nbytes + tc.nbytes
+            d2h += len(gids) * 4 * 8 + len(gids)
+        g.samples(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for gi, ci, tc, ob in per_wave:
+                g.eval_partial(gi, ci, tc, out=ob)
+                g.commit_improving()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": g.samples(reset=True) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "path": "dmr_eval_partial + dmr_commit_improving per wave, pinned "
+                                                       "host buffers"}
+
+    peaks, peak_kind = measured_peaks()
+    clock_max = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = n_sm * 128 * clock_max * 1e6 / 1e12  # T lane-ops/s
+    raster_s_per_step = raster_ms / 1e3 / args.steps
+    achieved = samples_per_step * ALG_OPS_PER_SAMPLE / raster_s_per_step / 1e12
+    bpv = 4 if args.storage == "f32" else 2
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-op/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "k_raster (rasterise + map + trilinear sample + SSD)",
+                "ops_per_sample": ALG_OPS_PER_SAMPLE,
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clock_max),
+                "raster_ms_per_step": raster_s_per_step * 1e3, "setup_ms_per_step": setup_ms / args.steps,
+                "touched_bytes_frac_of_hbm": value * 2 * bpv / 1e9 / hbm,
+                "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind}
+
+    variants = {}
+    if not args.no_variants and world == 1:
+        for st in ("f32", "bf16", "f16"):
+            if st == args.storage:
+                variants[st] = value
+                continue
+            gv, _ = build(st)
+            pv = gv.plan_generation(np.arange(C, dtype=np.int32), deltas)
+            for _ in range(3):
+                pv.run()
+            torch.cuda.synchronize()
+            gv.samples(reset=True)
+            tt = 0.0
+            for _ in range(max(3, args.steps // 2)):
+                flush.zero_()
+                ev0.record()
+                pv.run()
+                ev1.record()
+                torch.cuda.synchronize()
+                tt += ev0.elapsed_time(ev1)
+            variants[st] = gv.samples(reset=True) / (tt / 1e3)
+            pv.close()
+            gv.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pr, groups, waves, C, 7)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+                "data": "synthetic (seeded phantom, %s)" % pr["name"],
+                "config": {"workload": pr["desc"], "storage": args.storage, "population": C,
+                           "fos_groups": len(groups), "waves": len(waves), "mesh_pts": list(pr["mesh"]),
+                           "deform_model": "linear_elastic", "samples_per_step": samples_per_step,
+                           "l2": "flushed before every timed step (256 MiB write outside the event bracket)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": plan.launches * args.steps, "variants_samples_per_s": variants}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

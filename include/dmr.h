@@ -169,6 +169,11 @@ int dmr_plan_destroy(dmr_plan* plan);
 
 /* Kernel launches per dmr_plan_run (for accounting). */
 int dmr_plan_launches(const dmr_plan* plan, int* launches);
+/* Device time of the last completed dmr_plan_run, summed over its waves, of
+ * the geometry set-up kernels and of the rasterise-and-sample kernels (CUDA
+ * events recorded inside the graph, on the problem's stream).  Call after
+ * that run has finished (e.g. after synchronising the stream). */
+int dmr_plan_kernel_ms(const dmr_plan* plan, float* setup_ms, float* raster_ms);
 
 /* Tile shape of the rasterise-and-sample kernel: warps per CTA (4, 8, 16)
  * and voxels per warp iteration (32, 64, 128); both 0 = library default. */

@@ -187,6 +187,8 @@ struct dmr_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
+  // per wave: events before set-up, before and after the raster kernel
+  std::vector<cudaEvent_t> ev;
   // all waves' arrays (device), owned by the plan
   int* tt_trial = nullptr;
   int* tt_tet = nullptr;
@@ -956,6 +958,7 @@ int dmr_plan_destroy(dmr_plan* pl) {
   if (pl->p) cudaStreamSynchronize(pl->p->st);
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
+  for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
   dfree(pl->tt_trial); dfree(pl->tt_tet); dfree(pl->tt_slot); dfree(pl->tr_cand); dfree(pl->tr_first);
   dfree(pl->tr_ntt); dfree(pl->tr_group); dfree(pl->deltas); dfree(pl->cand_ptr); dfree(pl->cand_trials);
   pl->sc.release();
@@ -1043,6 +1046,12 @@ int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const d
     dmr_plan_destroy(pl);
     return fail(DMR_ECUDA, "plan upload failed");
   }
+  pl->ev.assign(3 * (size_t)nw, nullptr);
+  for (auto& e : pl->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      dmr_plan_destroy(pl);
+      return fail(DMR_ECUDA, "event create failed");
+    }
   // capture all waves into one graph
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1063,8 +1072,11 @@ int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const d
     b.gmax = G;
     const int* trg = pl->tr_group + w_tr0[w];
     launch_propose(p->d_prob, b, trg, p->d_gptr, p->d_gpts, pl->deltas + (size_t)w_tr0[w] * dl_per, cs);
+    cudaEventRecordWithFlags(pl->ev[3 * w], cs, cudaEventRecordExternal);
     launch_setup(p->d_prob, b, cs);
+    cudaEventRecordWithFlags(pl->ev[3 * w + 1], cs, cudaEventRecordExternal);
     launch_raster(p->d_prob, b, p->storage, p->warps, p->vpw, p->n_sm, cs);
+    cudaEventRecordWithFlags(pl->ev[3 * w + 2], cs, cudaEventRecordExternal);
     launches += 3;
     if (p->ng > 0) {
       launch_landmarks_partial(p->d_prob, b, cs);
@@ -1100,6 +1112,21 @@ int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const d
 int dmr_plan_run(dmr_plan* pl) {
   if (!pl || !pl->exec) return fail(DMR_EINVAL, "null plan");
   CU(cudaGraphLaunch(pl->exec, pl->p->st));
+  return DMR_OK;
+}
+
+int dmr_plan_kernel_ms(const dmr_plan* pl, float* setup_ms, float* raster_ms) {
+  if (!pl) return fail(DMR_EINVAL, "null plan");
+  float su = 0.f, ra = 0.f;
+  for (size_t w = 0; w + 2 < pl->ev.size(); w += 3) {
+    float a = 0.f, b = 0.f;
+    CU(cudaEventElapsedTime(&a, pl->ev[w], pl->ev[w + 1]));
+    CU(cudaEventElapsedTime(&b, pl->ev[w + 1], pl->ev[w + 2]));
+    su += a;
+    ra += b;
+  }
+  if (setup_ms) *setup_ms = su;
+  if (raster_ms) *raster_ms = ra;
   return DMR_OK;
 }
 

@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
         diff2 = fmaf(dl, tt_ + s, diff2);
       }
       float den = sqrtf(lt2) + sqrtf(ls2);
-      float dlen = den > 0.f ? diff2 / den : 0.f;
+      // zero-length edge pairs give 0; non-finite lengths propagate
+      float dlen = den > 0.f ? diff2 / den : (den == 0.f ? 0.f : den);
       acc = fmaf(dlen, dlen, acc);
     }
     def = (double)acc;

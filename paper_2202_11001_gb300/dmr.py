@@ -81,6 +81,7 @@ def load():
         "dmr_plan_run": [vp],
         "dmr_plan_destroy": [vp],
         "dmr_plan_launches": [vp, ip],
+        "dmr_plan_kernel_ms": [vp, ip, ip],
         "dmr_set_tile": [vp, i, i],
         "dmr_get_tile": [vp, ip, ip],
     }
@@ -100,7 +101,7 @@ def exported_symbols():
         "dmr_set_fos", "dmr_fos_info", "dmr_fos_waves", "dmr_eval_full", "dmr_eval_partial", "dmr_commit",
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
-        "dmr_plan_launches", "dmr_set_tile", "dmr_get_tile", "dmr_last_error",
+        "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_last_error",
     ]
 
 
@@ -352,6 +353,12 @@ class Plan:
 
     def run(self):
         _check(self.prob._lib.dmr_plan_run(self.h))
+
+    def kernel_ms(self):
+        """(set-up ms, raster ms) of the last completed run."""
+        su, ra = ctypes.c_float(), ctypes.c_float()
+        _check(self.prob._lib.dmr_plan_kernel_ms(self.h, ctypes.addressof(su), ctypes.addressof(ra)))
+        return su.value, ra.value
 
     def close(self):
         if getattr(self, "h", None):
