@@ -180,6 +180,24 @@ int dmr_plan_kernel_ms(const dmr_plan* plan, float* setup_ms, float* raster_ms);
 int dmr_set_tile(dmr_problem* p, int warps_per_cta, int voxels_per_warp);
 int dmr_get_tile(const dmr_problem* p, int* warps_per_cta, int* voxels_per_warp);
 
+/* Full evaluation of ONE candidate that allocates no memory.  The paper has
+ * no counterpart; this is a service for callers that must not allocate at
+ * evaluation time: code running while a stream is captured into a CUDA graph
+ * (cudaMalloc is not permitted during capture), optimiser loops that cannot
+ * afford the device synchronisation cudaMalloc/cudaFree imply, and processes
+ * whose device memory is owned by another allocator.
+ * coords: device [2][3][P] FP64 (both meshes of the candidate); obj_out:
+ * device [4] FP64, the same four values dmr_eval_full gives.  Limits:
+ * N_tet <= 4608 and n_guide <= 512, else DMR_EINVAL.  The problem's images,
+ * topology and population state are only read; the scratch is one fixed
+ * array of about 5.6 MB that every device holds from the first call until
+ * the process exits.  The first call on a device looks that array up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array: calls that may overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  Work is
+ * enqueued on the problem's stream; the call does not wait for it. */
+int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double* obj_out);
+
 const char* dmr_last_error(void);
 
 #ifdef __cplusplus

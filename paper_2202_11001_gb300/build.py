@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmr.so")
-SOURCES = ["dmr_api.cu", "dmr_kernels.cu"]
+SOURCES = ["dmr_api.cu", "dmr_kernels.cu", "dmr_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

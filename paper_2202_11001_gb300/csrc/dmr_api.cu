@@ -308,6 +308,22 @@ int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st, bool& ho
 
 }  // namespace
 
+namespace dmr {
+
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+int problem_view(const ::dmr_problem* p, DevProblem* hp, int* storage, int* warps, int* n_sm, cudaStream_t* st) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  *hp = p->hp;
+  *storage = p->storage;
+  *warps = p->warps;
+  *n_sm = p->n_sm;
+  *st = p->st;
+  return DMR_OK;
+}
+
+}  // namespace dmr
+
 extern "C" {
 
 const char* dmr_last_error(void) { return g_err.c_str(); }

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
+struct dmr_problem;
+
 namespace dmr {
 
 // Image storage types (match DMR_F32 / DMR_BF16 / DMR_F16 of dmr.h).
@@ -123,5 +127,11 @@ void launch_commit(const DevProblem* probs, const Batch& b, const uint8_t* accep
                    cudaStream_t st);
 void launch_propose(const DevProblem* probs, const Batch& b, const int* tr_group, const int* g_ptr, const int* g_pts,
                     const double* deltas, cudaStream_t st);
+
+// Host helpers shared by the C-ABI translation units (dmr_api.cu).
+// Record the calling thread's error message and return `code`.
+int set_error(int code, const std::string& msg);
+// Host copy of a problem's device descriptor plus its launch settings.
+int problem_view(const ::dmr_problem* p, DevProblem* hp, int* storage, int* warps, int* n_sm, cudaStream_t* st);
 
 }  // namespace dmr

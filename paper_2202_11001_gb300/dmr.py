@@ -83,6 +83,7 @@ def load():
         "dmr_plan_launches": [vp, ip],
         "dmr_plan_kernel_ms": [vp, ip, ip],
         "dmr_set_tile": [vp, i, i],
+        "dmr_eval_one_noalloc": [vp, vp, vp],
         "dmr_get_tile": [vp, ip, ip],
     }
     for name, args in sig.items():
@@ -101,7 +102,7 @@ def exported_symbols():
         "dmr_set_fos", "dmr_fos_info", "dmr_fos_waves", "dmr_eval_full", "dmr_eval_partial", "dmr_commit",
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
-        "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_last_error",
+        "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_eval_one_noalloc", "dmr_last_error",
     ]
 
 
@@ -327,6 +328,13 @@ class Problem:
         n = _check(self._lib.dmr_trial_out(self.h, int(k), tets.ctypes.data, cov.ctypes.data, ssd.ctypes.data,
                                            de.ctypes.data, fo.ctypes.data))
         return {"tets": tets[:n], "cov": cov[:n], "ssd": ssd[:n], "def": de[:n], "fold": fo[:n]}
+
+    def eval_one_noalloc(self, coords, out):
+        """Objectives of one candidate (device tensor [2, 3, P]) into ``out``
+        (device tensor [4]) without any allocation in the library."""
+        a = _Arg(coords, np.float64)
+        _check(self._lib.dmr_eval_one_noalloc(self.h, a.ptr, _addr(out)))
+        return out
 
     def samples(self, reset=False):
         v = ctypes.c_longlong()
