@@ -275,6 +275,7 @@ def main():
         return g, groups
 
     g, groups = build(args.storage)
+    tile_w, tile_v, tile_table = g.autotune()
     waves = g.waves()
     rng = np.random.default_rng(100 + rank)
     deltas = deltas_for(pr, groups, C, rng)
@@ -370,6 +371,7 @@ def main():
                 variants[st] = value
                 continue
             gv, _ = build(st)
+            gv.autotune()
             pv = gv.plan_generation(np.arange(C, dtype=np.int32), deltas)
             for _ in range(3):
                 pv.run()
@@ -399,6 +401,8 @@ def main():
                 "config": {"workload": pr["desc"], "storage": args.storage, "population": C,
                            "fos_groups": len(groups), "waves": len(waves), "mesh_pts": list(pr["mesh"]),
                            "deform_model": "linear_elastic", "samples_per_step": samples_per_step,
+                           "tile": {"warps_per_cta": tile_w, "voxels_per_warp": tile_v,
+                                    "autotune_ms": {"%dx%d" % k: round(v, 4) for k, v in tile_table.items()}},
                            "l2": "flushed before every timed step (256 MiB write outside the event bracket)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

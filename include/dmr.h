@@ -179,6 +179,14 @@ int dmr_plan_kernel_ms(const dmr_plan* plan, float* setup_ms, float* raster_ms);
  * and voxels per warp iteration (32, 64, 128); both 0 = library default. */
 int dmr_set_tile(dmr_problem* p, int warps_per_cta, int voxels_per_warp);
 int dmr_get_tile(const dmr_problem* p, int* warps_per_cta, int* voxels_per_warp);
+/* Autotuner: time the rasterise-and-sample kernel of every tile shape
+ * (warps per CTA x voxels per warp iteration, 3 x 3) on a full evaluation of
+ * the first n_cand committed candidates (n_cand <= 0: up to 16), keep the
+ * fastest as the problem's tile and report it; ms_table [9] (host, may be
+ * NULL) receives the times, row-major over warps {4,8,16} x voxels
+ * {32,64,128}.  Needs a population (dmr_eval_full first); does not change
+ * the committed state.  Plans created afterwards use the chosen tile. */
+int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, float* ms_table);
 
 /* Full evaluation of ONE candidate that allocates no memory.  The paper has
  * no counterpart; this is a service for callers that must not allocate at

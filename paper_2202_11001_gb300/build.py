@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmr.so")
-SOURCES = ["dmr_api.cu", "dmr_kernels.cu", "dmr_noalloc.cu"]
+SOURCES = ["dmr_api.cu", "dmr_kernels.cu", "dmr_noalloc.cu", "dmr_raster_f32.cu", "dmr_raster_bf16.cu",
+           "dmr_raster_f16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -42,6 +43,8 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_v: bool = Fa
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if ptxas_v:
         common += ["-Xptxas", "-v"]
+    if os.environ.get("DMR_RASTER_THREADS_PER_SM"):
+        common += ["-DDMR_RASTER_THREADS_PER_SM=%d" % int(os.environ["DMR_RASTER_THREADS_PER_SM"])]
     procs, objs = [], []
     for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))

@@ -968,6 +968,71 @@ int dmr_samples(dmr_problem* p, long long* samples, int reset) {
   return DMR_OK;
 }
 
+// ------------------------------------------------------------ autotuner
+int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, float* ms_table) {
+  if (!p) return fail(DMR_EINVAL, "null problem");
+  if (p->C == 0) return fail(DMR_ESTATE, "no population (call dmr_eval_full first)");
+  int nc = n_cand > 0 ? std::min(n_cand, p->C) : std::min(p->C, 16);
+  int rc;
+  if ((rc = p->sc.ensure(nc * p->ntet, nc, std::max(1, p->gmax), 2 * std::max(1, p->ng)))) return rc;
+  std::vector<int> tt_trial((size_t)nc * p->ntet), tt_tet((size_t)nc * p->ntet), tr_cand(nc), tr_first(nc), tr_ntt(nc);
+  for (int ci = 0; ci < nc; ++ci) {
+    tr_cand[ci] = ci;
+    tr_first[ci] = ci * p->ntet;
+    tr_ntt[ci] = p->ntet;
+    for (int t = 0; t < p->ntet; ++t) {
+      tt_trial[(size_t)ci * p->ntet + t] = ci;
+      tt_tet[(size_t)ci * p->ntet + t] = t;
+    }
+  }
+  int ntt = nc * p->ntet;
+  cudaStream_t st = p->st;
+  CU(cudaMemcpyAsync(p->sc.tt_trial, tt_trial.data(), sizeof(int) * ntt, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tt_tet, tt_tet.data(), sizeof(int) * ntt, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_cand, tr_cand.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_first, tr_first.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(p->sc.tr_ntt, tr_ntt.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+  Batch b = make_batch(p, p->sc, ntt, nc);
+  b.tt_slot = nullptr;
+  b.tr_coords = nullptr;
+  launch_setup(p->d_prob, b, st);
+  const int W[3] = {4, 8, 16}, V[3] = {32, 64, 128};
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 3.0e38f;
+  int bw = p->warps, bv = p->vpw;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      float tot = 0.f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaMemsetAsync(b.work, 0, sizeof(unsigned), st);
+        cudaEventRecord(e0, st);
+        launch_raster(p->d_prob, b, p->storage, W[i], V[j], p->n_sm, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;  // first launch warms up
+      }
+      float ms = tot / 3.f;
+      if (ms_table) ms_table[3 * i + j] = ms;
+      if (ms < best) {
+        best = ms;
+        bw = W[i];
+        bv = V[j];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(cudaGetLastError());
+  p->warps = bw;
+  p->vpw = bv;
+  if (best_warps) *best_warps = bw;
+  if (best_vpw) *best_vpw = bv;
+  return DMR_OK;
+}
+
 // ------------------------------------------------------------ generation plan
 int dmr_plan_destroy(dmr_plan* pl) {
   if (!pl) return DMR_OK;

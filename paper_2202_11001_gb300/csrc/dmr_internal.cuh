@@ -116,6 +116,9 @@ void launch_build_cells(const void* plain, int dtype, const int n[3], void* cell
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
 void launch_raster(const DevProblem* probs, const Batch& b, int storage_dtype, int warps, int vpw, int n_sm,
                    cudaStream_t st);
+void launch_raster_f32(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st);
+void launch_raster_bf16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st);
+void launch_raster_f16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st);
 void launch_locate_full(const DevProblem* probs, const DevProblem& host_pr, const Batch& b, int c0, int nc,
                         cudaStream_t st);
 void launch_reduce_full(const DevProblem* probs, int c0, int nc, const Batch& b, double* obj, cudaStream_t st);

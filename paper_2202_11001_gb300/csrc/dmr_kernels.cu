@@ -18,126 +18,9 @@
 #include <stdint.h>
 
 #include "dmr_internal.cuh"
+#include "dmr_device.cuh"
 
 namespace dmr {
-
-#define FULL_MASK 0xffffffffu
-
-// ------------------------------------------------------------ FP64 exact
-__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
-
-__device__ __forceinline__ void cross3d(const double a[3], const double b[3], double o[3]) {
-  o[0] = dsub(dmul(a[1], b[2]), dmul(a[2], b[1]));
-  o[1] = dsub(dmul(a[2], b[0]), dmul(a[0], b[2]));
-  o[2] = dsub(dmul(a[0], b[1]), dmul(a[1], b[0]));
-}
-__device__ __forceinline__ double dot3d(const double a[3], const double b[3]) {
-  return dadd(dmul(a[0], b[0]), dadd(dmul(a[1], b[1]), dmul(a[2], b[2])));
-}
-
-// Exact face predicate: canonical face (a,b,c) with inward sign s; p on the
-// inner side, or on the plane and the signed normal's first nonzero
-// component in (z, y, x) order is positive.
-__device__ __noinline__ bool face_in_exact(const double* A, const double* B, const double* Cc, int s,
-                                           const double p[3]) {
-  double u[3], w[3], n[3];
-  for (int k = 0; k < 3; ++k) {
-    u[k] = dsub(B[k], A[k]);
-    w[k] = dsub(Cc[k], A[k]);
-  }
-  cross3d(u, w, n);
-  double g = dadd(dmul(n[0], dsub(p[0], A[0])), dadd(dmul(n[1], dsub(p[1], A[1])), dmul(n[2], dsub(p[2], A[2]))));
-  double h = s > 0 ? g : -g;
-  if (h > 0) return true;
-  if (h == 0) {
-    double mz = s > 0 ? n[2] : -n[2];
-    double my = s > 0 ? n[1] : -n[1];
-    double mx = s > 0 ? n[0] : -n[0];
-    if (mz != 0) return mz > 0;
-    if (my != 0) return my > 0;
-    return mx > 0;
-  }
-  return false;
-}
-
-__device__ __forceinline__ int face_local(uint32_t fp, int f, int which) { return (fp >> (8 * f + 2 * which)) & 3; }
-__device__ __forceinline__ int face_sign(uint32_t fp, int f) { return ((fp >> (8 * f + 6)) & 1) ? -1 : 1; }
-
-// Exact face test of face f of the record's own tet at point p.
-__device__ __forceinline__ bool rec_face_in_exact(const ItemRec& r, uint32_t fp, int f, const double p[3]) {
-  int ia = face_local(fp, f, 0), ib = face_local(fp, f, 1), ic = face_local(fp, f, 2);
-  return face_in_exact(r.X[ia], r.X[ib], r.X[ic], face_sign(fp, f), p);
-}
-
-// FP64 mapped coordinate, the definition the black decision follows:
-// p' = (v + d0) + G (v - own_0).
-__device__ __noinline__ void map_exact(const ItemRec& r, const double v[3], double out[3]) {
-  double q[3];
-  for (int a = 0; a < 3; ++a) q[a] = dsub(v[a], r.X[0][a]);
-  for (int c = 0; c < 3; ++c)
-    out[c] = dadd(dadd(v[c], r.d0[c]),
-                  dadd(dmul(r.G64[c][0], q[0]), dadd(dmul(r.G64[c][1], q[1]), dmul(r.G64[c][2], q[2]))));
-}
-
-// ------------------------------------------------------------ float helpers
-#define MAGIC 12582912.0f /* 1.5 * 2^23 */
-#define MAGIC_BITS 0x4B400000
-
-// floor for |x| < 2^22 with two full-rate ALU ops: returns the float floor
-// and the integer floor + MAGIC_BITS (as raw bits).
-__device__ __forceinline__ float ffloor_magic(float x, int& ibits) {
-  float t = __fadd_rd(x, MAGIC);
-  ibits = __float_as_int(t);
-  return t - MAGIC;
-}
-
-__device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-__device__ __forceinline__ float f16lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffff))); }
-__device__ __forceinline__ float f16hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
-
-template <int ST>
-__device__ __forceinline__ float load_plain(const void* p, long i) {
-  if (ST == ST_F32) return __ldg((const float*)p + i);
-  unsigned short u = __ldg((const unsigned short*)p + i);
-  if (ST == ST_BF16) return __uint_as_float((uint32_t)u << 16);
-  return __half2float(__ushort_as_half(u));
-}
-
-__device__ __forceinline__ float load_plain_dyn(const void* p, int st, long i) {
-  if (st == ST_F32) return load_plain<ST_F32>(p, i);
-  if (st == ST_BF16) return load_plain<ST_BF16>(p, i);
-  return load_plain<ST_F16>(p, i);
-}
-
-// Trilinear interpolation of a corner-packed cell: corner index dx+2dy+4dz.
-template <int ST>
-__device__ __forceinline__ float cell_lerp(const void* cells, unsigned idx, float fx, float fy, float fz) {
-  float c0, c1, c2, c3, c4, c5, c6, c7;
-  if (ST == ST_F32) {
-    const float4* p = (const float4*)cells + 2 * (size_t)idx;
-    float4 a = __ldg(p), b = __ldg(p + 1);
-    c0 = a.x; c1 = a.y; c2 = a.z; c3 = a.w; c4 = b.x; c5 = b.y; c6 = b.z; c7 = b.w;
-  } else {
-    uint4 w = __ldg((const uint4*)cells + idx);
-    if (ST == ST_BF16) {
-      c0 = bf16lo(w.x); c1 = bf16hi(w.x); c2 = bf16lo(w.y); c3 = bf16hi(w.y);
-      c4 = bf16lo(w.z); c5 = bf16hi(w.z); c6 = bf16lo(w.w); c7 = bf16hi(w.w);
-    } else {
-      c0 = f16lo(w.x); c1 = f16hi(w.x); c2 = f16lo(w.y); c3 = f16hi(w.y);
-      c4 = f16lo(w.z); c5 = f16hi(w.z); c6 = f16lo(w.w); c7 = f16hi(w.w);
-    }
-  }
-  float a0 = fmaf(fx, c1 - c0, c0);
-  float a1 = fmaf(fx, c3 - c2, c2);
-  float a2 = fmaf(fx, c5 - c4, c4);
-  float a3 = fmaf(fx, c7 - c6, c6);
-  float b0 = fmaf(fy, a1 - a0, a0);
-  float b1 = fmaf(fy, a3 - a2, a2);
-  return fmaf(fz, b1 - b0, b0);
-}
 
 // ------------------------------------------------------------ image prep
 __global__ void k_convert(const void* src, int sdt, void* dst, int ddt, long n) {
@@ -181,6 +64,17 @@ __global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz,
     if (fv[c] == 0.0f) any0 = 1;
     else all0 = 0;
   }
+  // 4x4x4 voxel block (i-1 .. i+2 per axis, clamped): every support of a
+  // sample whose FP32 cell is this one lies inside it
+  int nb_all0 = 1, nb_none0 = 1;
+  for (int dz = -1; dz <= 2; ++dz)
+    for (int dy = -1; dy <= 2; ++dy)
+      for (int dx = -1; dx <= 2; ++dx) {
+        int x = min(max(i + dx, 0), nx - 1), y = min(max(j + dy, 0), ny - 1), z = min(max(k + dz, 0), nz - 1);
+        float v = load_plain_dyn(plain, st, ((long)z * ny + y) * nx + x);
+        if (v == 0.0f) nb_none0 = 0;
+        else nb_all0 = 0;
+      }
   if (st == ST_F32) {
     float4* p = (float4*)cells + 2 * id;
     p[0] = make_float4(fv[0], fv[1], fv[2], fv[3]);
@@ -193,7 +87,7 @@ __global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz,
     w.w = raw[6] | (raw[7] << 16);
     ((uint4*)cells)[id] = w;
   }
-  cflag[id] = (uint8_t)(any0 | (all0 << 1));
+  cflag[id] = (uint8_t)(any0 | (all0 << 1) | (nb_all0 << 2) | (nb_none0 << 3));
 }
 
 void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag, cudaStream_t st) {
@@ -441,6 +335,25 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
       kmax = fmaxf(kmax, fabsf(R.G[c][3]));
     }
     float M = (float)L * (1.0f + 3.0f * gmax) + kmax + 2.0f;
+    // bit1: the partner tet lies within [-0.75, n - 0.25] on every axis and
+    // the FP32 map error bound is far below 0.25 voxel, so no mapped voxel
+    // coordinate of this tet can leave [-1, n]
+    {
+      // fmin/fmax/fmaxf skip NaN, so finiteness is checked explicitly: a NaN
+      // partner vertex or map entry must take the clamped path
+      bool in = M < 4096.0f;
+      for (int a = 0; a < 3; ++a) {
+        double phi = par[0][a];
+        for (int i = 0; i < 4; ++i) {
+          in = in && isfinite(par[i][a]);
+          phi = fmax(phi, par[i][a]);
+        }
+        in = in && plo[a] >= -0.75 && phi <= (double)np[a] - 0.25;
+      }
+      for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 4; ++j) in = in && isfinite(R.G[c][j]);
+      if (in) R.flags |= 2;
+    }
     R.gx[0] = 1.0f + R.G[0][0];
     R.gx[1] = R.G[1][0];
     R.gx[2] = R.G[2][0];
@@ -465,337 +378,12 @@ void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ raster + sample
-struct WarpSmem {
-  ItemRec rec;
-  int2 meta[32];     // (excl prefix, own plain index of x0)
-  float4 pr0[32];    // mapped partner-relative coordinate of x0
-};
-
-__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(FULL_MASK, v, o);
-    if (lane >= o) v += y;
-  }
-  return v;
-}
-
-// y-range of slice z (relative to O) through the tet: min/max over edges
-// crossing the plane; a superset (slack) of the rows holding inside voxels.
-__device__ __forceinline__ void slice_yrange(const ItemRec& r, float zr, float& ylo, float& yhi) {
-  ylo = 3.0e38f;
-  yhi = -3.0e38f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = i + 1; j < 4; ++j) {
-      float zi = r.vr[i][2], zj = r.vr[j][2];
-      float yi = r.vr[i][1], yj = r.vr[j][1];
-      if ((zi - zr) * (zj - zr) <= 0.f) {
-        float y;
-        if (zj != zi) {
-          float tq = (zr - zi) / (zj - zi);
-          tq = fminf(fmaxf(tq, 0.f), 1.f);
-          y = fmaf(tq, yj - yi, yi);
-          ylo = fminf(ylo, y);
-          yhi = fmaxf(yhi, y);
-        } else {
-          ylo = fminf(ylo, fminf(yi, yj));
-          yhi = fmaxf(yhi, fmaxf(yi, yj));
-        }
-      }
-    }
-}
-
-// Exact span of row (y, z): x range (relative to O) inside all 4 faces.
-// Returns false when the row is empty.  Rows where the FP32 margin cannot
-// decide a face take the careful path: every voxel of the row range is
-// classified face by face, exactly where the margin does not decide.
-__device__ __noinline__ void span_careful(const ItemRec& r, uint32_t fp, int xl, int xh, int yi, int zi,
-                                          int& lo, int& hi) {
-  const float yr = (float)yi, zr = (float)zi;
-  int first = xh + 1, last = xl - 1;
-  for (int x = xl; x <= xh; ++x) {
-    bool in = true;
-    for (int f = 0; f < 4 && in; ++f) {
-      float c = fmaf(r.fa[f][1], yr, fmaf(r.fa[f][2], zr, r.fa[f][3]));
-      float h = fmaf(r.fa[f][0], (float)x, c);
-      float mu = r.fm[f][0];
-      if (h > mu) continue;
-      if (h < -mu) {
-        in = false;
-        break;
-      }
-      double p[3] = {(double)(x + r.O[0]), (double)(yi + r.O[1]), (double)(zi + r.O[2])};
-      in = rec_face_in_exact(r, fp, f, p);
-    }
-    if (in) {
-      first = min(first, x);
-      last = max(last, x);
-    }
-  }
-  lo = first;
-  hi = last;
-}
-
-__device__ __forceinline__ void row_span(const ItemRec& r, uint32_t fp, int xl, int xh, int yi, int zi, int& lo,
-                                         int& hi) {
-  const float yr = (float)yi, zr = (float)zi;
-  lo = xl;
-  hi = xh;
-  bool ok = true;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    float Ax = r.fa[f][0];
-    float c = fmaf(r.fa[f][1], yr, fmaf(r.fa[f][2], zr, r.fa[f][3]));
-    float mu = r.fm[f][0];
-    if (Ax == 0.f) {
-      if (c < -mu) hi = xl - 1;
-      else if (!(c > mu)) ok = false;
-      continue;
-    }
-    float th = -c * r.fm[f][1];
-    th = fminf(fmaxf(th, (float)(xl - 1)), (float)(xh + 1));
-    int kb;
-    float kf = ffloor_magic(th, kb);
-    int kint = kb - MAGIC_BITS;
-    float h0 = fmaf(Ax, kf, c);
-    float h1 = fmaf(Ax, kf + 1.0f, c);
-    if (Ax > 0.f) {
-      ok = ok && (kint < xl || h0 < -mu) && (kint + 1 > xh || h1 > mu);
-      lo = max(lo, kint + 1);
-    } else {
-      ok = ok && (kint < xl || h0 > mu) && (kint + 1 > xh || h1 < -mu);
-      hi = min(hi, kint);
-    }
-  }
-  if (!ok) span_careful(r, fp, xl, xh, yi, zi, lo, hi);
-}
-
-// Black decision of one sample where the FP32 cell cannot decide it: FP64
-// mapped coordinate (definition), its support, and the plain partner image.
-__device__ __noinline__ bool black_exact(const ItemRec& r, const DevProblem& pr, int x, int y, int z) {
-  double v[3] = {(double)x, (double)y, (double)z};
-  double p[3];
-  map_exact(r, v, p);
-  int dp = 1 - r.dir;
-  const int* n = pr.n[dp];
-  int i0[3], i1[3];
-  bool sup1[3];
-  for (int a = 0; a < 3; ++a) {
-    double q = fmin(fmax(p[a], -1.0), (double)n[a]);
-    double fl = floor(q);
-    int i = (int)fl;
-    sup1[a] = (q - fl) > 0;
-    i0[a] = min(max(i, 0), n[a] - 1);
-    i1[a] = min(max(i + 1, 0), n[a] - 1);
-  }
-  for (int c = 0; c < 8; ++c) {
-    int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-    if ((dx && !sup1[0]) || (dy && !sup1[1]) || (dz && !sup1[2])) continue;
-    long li = ((long)(dz ? i1[2] : i0[2]) * n[1] + (dy ? i1[1] : i0[1])) * n[0] + (dx ? i1[0] : i0[0]);
-    if (load_plain_dyn(pr.plain[dp], pr.dtype, li) != 0.0f) return false;
-  }
-  return true;
-}
-
-template <int ST, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_raster(const DevProblem* __restrict__ probs, Batch b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem* ws = (WarpSmem*)smem_raw + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  const unsigned lemask = 0xffffffffu >> (31 - lane);
-  const int n_items = 2 * b.n_tt;
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = (int)atomicAdd(b.work, 1u);
-    item = __shfl_sync(FULL_MASK, item, 0);
-    if (item >= n_items) break;
-    // stage the record in shared memory
-    {
-      const int4* src = (const int4*)(b.rec + item);
-      int4* dst = (int4*)&ws->rec;
-      constexpr int NW = sizeof(ItemRec) / 16;
-      for (int i = lane; i < NW; i += 32) dst[i] = __ldg(src + i);
-    }
-    __syncwarp();
-    const ItemRec& r = ws->rec;
-    float sum = 0.f, comp = 0.f;
-    int cov = 0;
-    if (r.flags & 1) {
-      const DevProblem& pr = probs[r.prob];
-      const int d = r.dir;
-      const uint32_t fp = pr.fperm[r.tet];
-      const void* own_img = pr.plain[d];
-      const void* cells = pr.cells[1 - d];
-      const uint8_t* cflag = pr.cflag[1 - d];
-      const int nxo = pr.n[d][0], nyo = pr.n[d][1];
-      const int Sy = pr.n[1 - d][0] + 2, Sz = (pr.n[1 - d][1] + 2) * Sy;
-      const bool black = pr.black_rule != 0;
-      const float G00 = r.G[0][0], G01 = r.G[0][1], G02 = r.G[0][2], K0 = r.G[0][3];
-      const float G10 = r.G[1][0], G11 = r.G[1][1], G12 = r.G[1][2], K1 = r.G[1][3];
-      const float G20 = r.G[2][0], G21 = r.G[2][1], G22 = r.G[2][2], K2 = r.G[2][3];
-      const float gxx = r.gx[0], gxy = r.gx[1], gxz = r.gx[2], delta = r.gx[3];
-      const float clx = r.clo[0], cly = r.clo[1], clz = r.clo[2];
-      const float chx = r.chi[0], chy = r.chi[1], chz = r.chi[2];
-      const unsigned cbase = r.cbase;
-      const int Ox = r.O[0], Oy = r.O[1], Oz = r.O[2];
-      const int xl = r.b0[0] - Ox, xh = r.b1[0] - Ox;
-      const int by0 = r.b0[1], by1 = r.b1[1];
-      for (int zb = r.b0[2]; zb <= r.b1[2]; zb += 32) {
-        // slices -> y ranges
-        int z = zb + lane;
-        int ycnt = 0, ylo = 0;
-        if (z <= r.b1[2]) {
-          float ylf, yhf;
-          slice_yrange(r, (float)(z - Oz), ylf, yhf);
-          float slack = 1.0f / 256.0f + 1e-5f * fabsf(yhf);
-          int y0 = max(by0, (int)ceilf(ylf - slack) + Oy);
-          int y1 = min(by1, (int)floorf(yhf + slack) + Oy);
-          if (ylf <= yhf && y1 >= y0) {
-            ylo = y0;
-            ycnt = y1 - y0 + 1;
-          }
-        }
-        int yincl = warp_incl_scan(ycnt, lane);
-        int yexcl = yincl - ycnt;
-        const int R = __shfl_sync(FULL_MASK, yincl, 31);
-        for (int rb = 0; rb < R; rb += 32) {
-          const int rr = rb + lane;
-          const bool has_row = rr < R;
-          const int rq = has_row ? rr : R - 1;
-          // slice holding row rq: the last lane with yexcl <= rq
-          int s = 0;
-#pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            const int cs = s + step;
-            const int e = __shfl_sync(FULL_MASK, yexcl, cs & 31);
-            if (cs < 32 && e <= rq) s = cs;
-          }
-          const int e_s = __shfl_sync(FULL_MASK, yexcl, s);
-          const int yl_s = __shfl_sync(FULL_MASK, ylo, s);
-          const int zrow = zb + s;
-          const int yrow = yl_s + (rq - e_s);
-          int xcnt = 0, x0 = 0;
-          if (has_row) {
-            int lo, hi;
-            row_span(r, fp, xl, xh, yrow - Oy, zrow - Oz, lo, hi);
-            if (hi >= lo) {
-              xcnt = hi - lo + 1;
-              x0 = lo + Ox;
-            }
-          }
-          // compact non-empty rows and publish them
-          const unsigned nz = __ballot_sync(FULL_MASK, xcnt > 0);
-          const int cidx = __popc(nz & (lemask >> 1));
-          const int xincl = warp_incl_scan(xcnt, lane);
-          const int xexcl = xincl - xcnt;
-          const int T = __shfl_sync(FULL_MASK, xincl, 31);
-          if (xcnt > 0) {
-            float vx = (float)(x0 - Ox), vy = (float)(yrow - Oy), vz = (float)(zrow - Oz);
-            float px = vx + fmaf(G00, vx, fmaf(G01, vy, fmaf(G02, vz, K0)));
-            float py = vy + fmaf(G10, vx, fmaf(G11, vy, fmaf(G12, vz, K1)));
-            float pz = vz + fmaf(G20, vx, fmaf(G21, vy, fmaf(G22, vz, K2)));
-            ws->meta[cidx] = make_int2(xexcl, (zrow * nyo + yrow) * nxo + x0);
-            ws->pr0[cidx] = make_float4(px, py, pz, 0.f);
-          }
-          __syncwarp();
-          int rows_before = 0;
-          for (int vb = 0; vb < T; vb += 32) {
-            unsigned bit = (xcnt > 0 && xexcl >= vb && xexcl < vb + 32) ? (1u << (xexcl - vb)) : 0u;
-            const unsigned sm = __reduce_or_sync(FULL_MASK, bit);
-            const int v = vb + lane;
-            const int row = rows_before + __popc(sm & lemask) - 1;
-            rows_before += __popc(sm);
-            if (v < T) {
-              const int2 mt = ws->meta[row];
-              const float4 p0 = ws->pr0[row];
-              const int dx = v - mt.x;
-              const float dxf = __int_as_float(dx + MAGIC_BITS) - MAGIC;
-              float px = fminf(fmaxf(fmaf(dxf, gxx, p0.x), clx), chx);
-              float py = fminf(fmaxf(fmaf(dxf, gxy, p0.y), cly), chy);
-              float pz = fminf(fmaxf(fmaf(dxf, gxz, p0.z), clz), chz);
-              int ix, iy, iz;
-              float flx = ffloor_magic(px, ix), fly = ffloor_magic(py, iy), flz = ffloor_magic(pz, iz);
-              float fx = px - flx, fy = py - fly, fz = pz - flz;
-              unsigned cidx2 = cbase + (unsigned)iz * (unsigned)Sz + (unsigned)iy * (unsigned)Sy + (unsigned)ix;
-              float s = cell_lerp<ST>(cells, cidx2, fx, fy, fz);
-              float o = load_plain<ST>(own_img, mt.y + dx);
-              float dd = o - s;
-              float d2 = dd * dd;
-              if (black) {
-                const uint8_t cf = __ldg(cflag + cidx2);
-                bool own0 = (o == 0.0f);
-                bool blk = false;
-                if (cf & 1) {
-                  bool nearp = fminf(fminf(fx, fy), fz) < delta || fmaxf(fmaxf(fx, fy), fz) > 1.0f - delta;
-                  if (!nearp) {
-                    blk = (cf & 2) != 0;
-                  } else {
-                    const int xa = (mt.y + dx) % nxo;
-                    const int rem = (mt.y + dx) / nxo;
-                    blk = black_exact(r, pr, xa, rem % nyo, rem / nyo);
-                  }
-                }
-                if (own0 != blk) d2 = 1.0f;
-              }
-              // Kahan
-              float yk = d2 - comp;
-              float tk = sum + yk;
-              comp = (tk - sum) - yk;
-              sum = tk;
-              ++cov;
-            }
-          }
-          __syncwarp();
-        }
-      }
-    }
-    // error-free warp reduction of (sum, -comp)
-    float hi = sum, lo = -comp;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      float oh = __shfl_xor_sync(FULL_MASK, hi, o);
-      float ol = __shfl_xor_sync(FULL_MASK, lo, o);
-      float sh = hi + oh;
-      float bb = sh - hi;
-      float err = (hi - (sh - bb)) + (oh - bb);
-      hi = sh;
-      lo = lo + ol + err;
-    }
-    int covt = __reduce_add_sync(FULL_MASK, cov);
-    if (lane == 0) {
-      b.o_ssd[item] = (double)hi + (double)lo;
-      b.o_cov[item] = covt;
-    }
-    __syncwarp();
-  }
-}
-
 void launch_raster(const DevProblem* probs, const Batch& b, int st_dtype, int warps, int vpw, int n_sm,
                    cudaStream_t st) {
-  (void)vpw;
   if (b.n_tt <= 0) return;
-  int threads = 32 * warps;
-  size_t smem = sizeof(WarpSmem) * warps;
-  long items = 2L * b.n_tt;
-  int per_sm = 2048 / threads;
-  long blocks = (long)n_sm * per_sm;
-  long need = (items + warps - 1) / warps;
-  if (blocks > need) blocks = need;
-  if (blocks < 1) blocks = 1;
-#define DMR_RASTER_LAUNCH(ST_, W_) k_raster<ST_, W_><<<(unsigned)blocks, threads, smem, st>>>(probs, b)
-#define DMR_RASTER_BY_WARPS(ST_)          \
-  if (warps == 4) DMR_RASTER_LAUNCH(ST_, 4);  \
-  else if (warps == 16) DMR_RASTER_LAUNCH(ST_, 16); \
-  else DMR_RASTER_LAUNCH(ST_, 8)
-  if (st_dtype == ST_F32) {
-    DMR_RASTER_BY_WARPS(ST_F32);
-  } else if (st_dtype == ST_BF16) {
-    DMR_RASTER_BY_WARPS(ST_BF16);
-  } else {
-    DMR_RASTER_BY_WARPS(ST_F16);
-  }
+  if (st_dtype == ST_F32) launch_raster_f32(probs, b, warps, vpw, n_sm, st);
+  else if (st_dtype == ST_BF16) launch_raster_bf16(probs, b, warps, vpw, n_sm, st);
+  else launch_raster_f16(probs, b, warps, vpw, n_sm, st);
 }
 
 // ------------------------------------------------------------ landmarks

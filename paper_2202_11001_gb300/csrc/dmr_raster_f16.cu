@@ -1,0 +1,10 @@
+// Rasterise-and-sample kernels for f16 image storage (see dmr_device.cuh).
+#include "dmr_device.cuh"
+
+namespace dmr {
+
+void launch_raster_f16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st) {
+  raster_launch<ST_F16>(probs, b, warps, vpw, n_sm, st);
+}
+
+}  // namespace dmr

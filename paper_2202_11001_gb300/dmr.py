@@ -84,6 +84,7 @@ def load():
         "dmr_plan_kernel_ms": [vp, ip, ip],
         "dmr_set_tile": [vp, i, i],
         "dmr_eval_one_noalloc": [vp, vp, vp],
+        "dmr_autotune": [vp, i, ip, ip, ip],
         "dmr_get_tile": [vp, ip, ip],
     }
     for name, args in sig.items():
@@ -102,7 +103,7 @@ def exported_symbols():
         "dmr_set_fos", "dmr_fos_info", "dmr_fos_waves", "dmr_eval_full", "dmr_eval_partial", "dmr_commit",
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
-        "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_eval_one_noalloc", "dmr_last_error",
+        "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_eval_one_noalloc", "dmr_last_error",
     ]
 
 
@@ -244,6 +245,21 @@ class Problem:
 
     def set_tile(self, warps=0, voxels_per_warp=0):
         _check(self._lib.dmr_set_tile(self.h, int(warps), int(voxels_per_warp)))
+
+    def tile(self):
+        w, v = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.dmr_get_tile(self.h, ctypes.addressof(w), ctypes.addressof(v)))
+        return w.value, v.value
+
+    def autotune(self, n_cand=0):
+        """Pick the fastest raster tile shape; returns (warps, voxels per warp,
+        {(warps, voxels): ms})."""
+        w, v = ctypes.c_int(), ctypes.c_int()
+        tab = (ctypes.c_float * 9)()
+        _check(self._lib.dmr_autotune(self.h, int(n_cand), ctypes.addressof(w), ctypes.addressof(v),
+                                      ctypes.addressof(tab)))
+        table = {(W, V): tab[3 * i + j] for i, W in enumerate((4, 8, 16)) for j, V in enumerate((32, 64, 128))}
+        return w.value, v.value, table
 
     # -- FOS --------------------------------------------------------------
     def set_fos(self, groups):

@@ -165,11 +165,19 @@ def test_folds_nan_and_border_violations():
         assert_terms_match(g, o, k)
 
 
-def test_tile_shapes_same_result():
-    pr = synth.sphere_pair(seed=9, C=3)
+def test_tile_shapes_same_result_and_autotune():
+    """Every tile shape (warps per CTA x voxels per warp iteration) gives
+    bit-identical results; the autotuner picks one of them."""
+    pr = synth.ellipsoid_pair(seed=9, C=3)
     g, o = make_pair(pr)
     ref = g.eval_full(pr["coords"])
+    assert_obj_close(ref, o.eval_full(pr["coords"]))
     for w in (4, 8, 16):
-        g.set_tile(w, 32)
-        out = g.eval_full(pr["coords"])
-        assert np.array_equal(out, ref)
+        for v in (32, 64, 128):
+            g.set_tile(w, v)
+            out = g.eval_full(pr["coords"])
+            assert np.array_equal(out, ref), (w, v)
+    bw, bv, table = g.autotune()
+    assert (bw, bv) in table and all(t > 0 for t in table.values())
+    assert g.tile() == (bw, bv)
+    assert np.array_equal(g.eval_full(pr["coords"]), ref)
