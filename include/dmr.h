@@ -52,6 +52,7 @@ extern "C" {
 
 typedef struct dmr_problem dmr_problem;
 typedef struct dmr_plan dmr_plan;
+typedef struct dmr_batch dmr_batch;
 
 enum {
   DMR_OK = 0,
@@ -165,6 +166,21 @@ int dmr_samples(dmr_problem* p, long long* samples, int reset);
 int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const double* deltas,
                         dmr_plan** out);
 int dmr_plan_run(dmr_plan* plan);
+
+/* Batches of independent registration problems of uneven size (images,
+ * meshes, populations): every kernel of a generation plan serves all of
+ * them at once, one persistent launch per kernel and wave, all captured in
+ * one CUDA graph.  probs: n handles (host array) on one device, one storage
+ * dtype, each with a registered FOS and a population; the batch borrows
+ * them (destroy the batch before its problems).  The plan runs on the first
+ * problem's stream and uses its tile shape. */
+int dmr_batch_create(int n, dmr_problem* const* probs, dmr_batch** out);
+int dmr_batch_destroy(dmr_batch* batch);
+/* Per problem q: n_cand[q] candidates cand_ids[q] and deltas[q]
+ * [n_groups_q][n_cand[q]][2][3][G_q] (host or device), as in
+ * dmr_plan_generation.  Wave w of the plan runs wave w of every problem. */
+int dmr_batch_plan_generation(dmr_batch* batch, const int* n_cand, const int* const* cand_ids,
+                              const double* const* deltas, dmr_plan** out);
 int dmr_plan_destroy(dmr_plan* plan);
 
 /* Kernel launches per dmr_plan_run (for accounting). */

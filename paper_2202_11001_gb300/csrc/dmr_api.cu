@@ -197,6 +197,7 @@ struct dmr_plan {
   int* tr_first = nullptr;
   int* tr_ntt = nullptr;
   int* tr_group = nullptr;
+  int* tr_prob = nullptr;
   double* deltas = nullptr;
   int* cand_ptr = nullptr;
   int* cand_trials = nullptr;
@@ -1041,70 +1042,80 @@ int dmr_plan_destroy(dmr_plan* pl) {
   if (pl->graph) cudaGraphDestroy(pl->graph);
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
   dfree(pl->tt_trial); dfree(pl->tt_tet); dfree(pl->tt_slot); dfree(pl->tr_cand); dfree(pl->tr_first);
-  dfree(pl->tr_ntt); dfree(pl->tr_group); dfree(pl->deltas); dfree(pl->cand_ptr); dfree(pl->cand_trials);
+  dfree(pl->tr_ntt); dfree(pl->tr_group); dfree(pl->tr_prob); dfree(pl->deltas); dfree(pl->cand_ptr);
+  dfree(pl->cand_trials);
   pl->sc.release();
   delete pl;
   return DMR_OK;
 }
 
-int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const double* deltas, dmr_plan** out) {
-  if (!p || !cand_ids || !deltas || !out) return fail(DMR_EINVAL, "null argument");
-  *out = nullptr;
-  if (p->n_groups == 0) return fail(DMR_ESTATE, "no FOS registered");
-  if (p->C == 0) return fail(DMR_ESTATE, "no population (call dmr_eval_full first)");
-  if (n_cand < 1 || n_cand > p->C) return fail(DMR_EINVAL, "n_cand out of range");
-  std::vector<int> cid(n_cand);
-  CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n_cand, cudaMemcpyDefault));
-  {
-    std::vector<int> s(cid);
-    std::sort(s.begin(), s.end());
-    for (int k = 0; k < n_cand; ++k) {
-      if (s[k] < 0 || s[k] >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
-      if (k && s[k] == s[k - 1]) return fail(DMR_EINVAL, "duplicate candidate id");
-    }
+namespace {
+
+// One generation of partial evaluations for one or more problems, captured
+// into a CUDA graph.  Wave w of the plan holds wave w of every problem that
+// has one; trials are ordered (problem, candidate, group).  deltas[q] is the
+// host copy [n_groups][n_cand][2][3][G_q] of problem q.
+int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs, const int* d_gptr,
+               const int* d_gpts, const std::vector<int>& goff, const std::vector<std::vector<int>>& cands,
+               const std::vector<std::vector<double>>& deltas, dmr_plan** out) {
+  dmr_problem* p0 = probs[0];
+  const int nq = (int)probs.size();
+  int G = 1, nw = 0, acap = 2;
+  for (dmr_problem* p : probs) {
+    G = std::max(G, p->gmax);
+    nw = std::max(nw, (int)p->wave_ptr.size() - 1);
+    acap = std::max(acap, 2 * p->ng);
   }
-  const int G = p->gmax;
-  const int nw = (int)p->wave_ptr.size() - 1;
-  size_t dl_per = (size_t)6 * G;
-  std::vector<double> hd((size_t)p->n_groups * n_cand * dl_per);
-  CU(cudaMemcpy(hd.data(), deltas, sizeof(double) * hd.size(), cudaMemcpyDefault));
   dmr_plan* pl = new (std::nothrow) dmr_plan();
   if (!pl) return fail(DMR_ENOMEM, "host allocation failed");
-  pl->p = p;
-  // arrays for all waves: trials ordered (wave, candidate, group)
-  std::vector<int> tt_trial, tt_tet, tr_cand, tr_first, tr_ntt, tr_group, cptr, ctr;
+  pl->p = p0;
+  std::vector<int> tt_trial, tt_tet, tr_cand, tr_first, tr_ntt, tr_group, tr_prob, cptr, ctr;
   std::vector<uint32_t> tt_slot;
   std::vector<double> dl;
-  std::vector<int> w_tt0, w_ntt, w_tr0, w_ntr, w_c0;
+  std::vector<int> w_tt0, w_ntt, w_tr0, w_ntr, w_c0, w_nlist;
   int max_tt = 0, max_tr = 0;
+  const size_t dl_per = (size_t)6 * G;
   for (int w = 0; w < nw; ++w) {
     w_tt0.push_back((int)tt_trial.size());
     w_tr0.push_back((int)tr_cand.size());
     w_c0.push_back((int)cptr.size());
-    int k = 0, ttw = 0;
-    for (int ci = 0; ci < n_cand; ++ci) {
-      cptr.push_back(k);
-      for (int gi = p->wave_ptr[w]; gi < p->wave_ptr[w + 1]; ++gi, ++k) {
-        int g = p->wave_groups[gi];
-        ctr.push_back(k);
-        tr_cand.push_back(cid[ci]);
-        tr_group.push_back(g);
-        tr_first.push_back(ttw);
-        int n = p->g_tptr[g + 1] - p->g_tptr[g];
-        tr_ntt.push_back(n);
-        for (int j = 0; j < n; ++j) {
-          tt_trial.push_back(k);
-          tt_tet.push_back(p->g_tets[p->g_tptr[g] + j]);
-          tt_slot.push_back(p->g_slot[p->g_tptr[g] + j]);
+    int k = 0, ttw = 0, nlist = 0;
+    for (int q = 0; q < nq; ++q) {
+      dmr_problem* p = probs[q];
+      if (w >= (int)p->wave_ptr.size() - 1) continue;
+      const int Gq = p->gmax;
+      const int nc = (int)cands[q].size();
+      for (int ci = 0; ci < nc; ++ci) {
+        cptr.push_back(k);
+        ++nlist;
+        for (int gi = p->wave_ptr[w]; gi < p->wave_ptr[w + 1]; ++gi, ++k) {
+          const int g = p->wave_groups[gi];
+          ctr.push_back(k);
+          tr_cand.push_back(cands[q][ci]);
+          tr_group.push_back(goff[q] + g);
+          tr_prob.push_back(q);
+          tr_first.push_back(ttw);
+          const int n = p->g_tptr[g + 1] - p->g_tptr[g];
+          tr_ntt.push_back(n);
+          for (int j = 0; j < n; ++j) {
+            tt_trial.push_back(k);
+            tt_tet.push_back(p->g_tets[p->g_tptr[g] + j]);
+            tt_slot.push_back(p->g_slot[p->g_tptr[g] + j]);
+          }
+          ttw += n;
+          // [2][3][Gq] of the problem -> [2][3][G] of the plan
+          const double* src = &deltas[q][((size_t)g * nc + ci) * 6 * Gq];
+          size_t base = dl.size();
+          dl.resize(base + dl_per, 0.0);
+          for (int ma = 0; ma < 6; ++ma)
+            for (int j = 0; j < Gq; ++j) dl[base + (size_t)ma * G + j] = src[(size_t)ma * Gq + j];
         }
-        ttw += n;
-        const double* src = &hd[((size_t)g * n_cand + ci) * dl_per];
-        dl.insert(dl.end(), src, src + dl_per);
       }
     }
     cptr.push_back(k);
     w_ntt.push_back(ttw);
     w_ntr.push_back(k);
+    w_nlist.push_back(nlist);
     max_tt = std::max(max_tt, ttw);
     max_tr = std::max(max_tr, k);
   }
@@ -1112,9 +1123,9 @@ int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const d
   if ((rc = dalloc(&pl->tt_trial, tt_trial.size())) || (rc = dalloc(&pl->tt_tet, tt_tet.size())) ||
       (rc = dalloc(&pl->tt_slot, tt_slot.size())) || (rc = dalloc(&pl->tr_cand, tr_cand.size())) ||
       (rc = dalloc(&pl->tr_first, tr_first.size())) || (rc = dalloc(&pl->tr_ntt, tr_ntt.size())) ||
-      (rc = dalloc(&pl->tr_group, tr_group.size())) || (rc = dalloc(&pl->deltas, dl.size())) ||
-      (rc = dalloc(&pl->cand_ptr, cptr.size())) || (rc = dalloc(&pl->cand_trials, ctr.size())) ||
-      (rc = pl->sc.ensure(max_tt, max_tr, G, 2 * std::max(1, p->ng)))) {
+      (rc = dalloc(&pl->tr_group, tr_group.size())) || (rc = dalloc(&pl->tr_prob, tr_prob.size())) ||
+      (rc = dalloc(&pl->deltas, dl.size())) || (rc = dalloc(&pl->cand_ptr, cptr.size())) ||
+      (rc = dalloc(&pl->cand_trials, ctr.size())) || (rc = pl->sc.ensure(max_tt, max_tr, G, acap))) {
     dmr_plan_destroy(pl);
     return rc;
   }
@@ -1122,8 +1133,9 @@ int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const d
   if (up(pl->tt_trial, tt_trial.data(), 4 * tt_trial.size()) || up(pl->tt_tet, tt_tet.data(), 4 * tt_tet.size()) ||
       up(pl->tt_slot, tt_slot.data(), 4 * tt_slot.size()) || up(pl->tr_cand, tr_cand.data(), 4 * tr_cand.size()) ||
       up(pl->tr_first, tr_first.data(), 4 * tr_first.size()) || up(pl->tr_ntt, tr_ntt.data(), 4 * tr_ntt.size()) ||
-      up(pl->tr_group, tr_group.data(), 4 * tr_group.size()) || up(pl->deltas, dl.data(), 8 * dl.size()) ||
-      up(pl->cand_ptr, cptr.data(), 4 * cptr.size()) || up(pl->cand_trials, ctr.data(), 4 * ctr.size())) {
+      up(pl->tr_group, tr_group.data(), 4 * tr_group.size()) || up(pl->tr_prob, tr_prob.data(), 4 * tr_prob.size()) ||
+      up(pl->deltas, dl.data(), 8 * dl.size()) || up(pl->cand_ptr, cptr.data(), 4 * cptr.size()) ||
+      up(pl->cand_trials, ctr.data(), 4 * ctr.size())) {
     dmr_plan_destroy(pl);
     return fail(DMR_ECUDA, "plan upload failed");
   }
@@ -1133,40 +1145,44 @@ int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const d
       dmr_plan_destroy(pl);
       return fail(DMR_ECUDA, "event create failed");
     }
-  // capture all waves into one graph
+  bool any_ng = false;
+  for (dmr_problem* p : probs) any_ng = any_ng || p->ng > 0;
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
     dmr_plan_destroy(pl);
     return fail(DMR_ECUDA, "stream create failed");
   }
-  cudaStreamSynchronize(p->st);
+  for (dmr_problem* p : probs) cudaStreamSynchronize(p->st);
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   int launches = 0;
   for (int w = 0; w < nw && e == cudaSuccess; ++w) {
-    Batch b = make_batch(p, pl->sc, w_ntt[w], w_ntr[w]);
+    Batch b = make_batch(p0, pl->sc, w_ntt[w], w_ntr[w]);
     b.tt_trial = pl->tt_trial + w_tt0[w];
     b.tt_tet = pl->tt_tet + w_tt0[w];
     b.tt_slot = pl->tt_slot + w_tt0[w];
     b.tr_cand = pl->tr_cand + w_tr0[w];
     b.tr_first = pl->tr_first + w_tr0[w];
     b.tr_ntt = pl->tr_ntt + w_tr0[w];
+    b.tr_prob = pl->tr_prob + w_tr0[w];
     b.gmax = G;
+    b.aff_cap = pl->sc.aff_cap;
+    b.aff_n = any_ng ? pl->sc.aff_n : nullptr;
     const int* trg = pl->tr_group + w_tr0[w];
-    launch_propose(p->d_prob, b, trg, p->d_gptr, p->d_gpts, pl->deltas + (size_t)w_tr0[w] * dl_per, cs);
+    launch_propose(d_probs, b, trg, d_gptr, d_gpts, pl->deltas + (size_t)w_tr0[w] * dl_per, cs);
     cudaEventRecordWithFlags(pl->ev[3 * w], cs, cudaEventRecordExternal);
-    launch_setup(p->d_prob, b, cs);
+    launch_setup(d_probs, b, cs);
     cudaEventRecordWithFlags(pl->ev[3 * w + 1], cs, cudaEventRecordExternal);
-    launch_raster(p->d_prob, b, p->storage, p->warps, p->vpw, p->n_sm, cs);
+    launch_raster(d_probs, b, p0->storage, p0->warps, p0->vpw, p0->n_sm, cs);
     cudaEventRecordWithFlags(pl->ev[3 * w + 2], cs, cudaEventRecordExternal);
     launches += 3;
-    if (p->ng > 0) {
-      launch_landmarks_partial(p->d_prob, b, cs);
+    if (any_ng) {
+      launch_landmarks_partial(d_probs, b, cs);
       ++launches;
     }
-    launch_reduce_partial(p->d_prob, b, cs);
-    launch_accept(p->d_prob, b, pl->sc.accept, cs);
-    launch_commit(p->d_prob, b, pl->sc.accept, trg, p->d_gptr, p->d_gpts, pl->cand_ptr + w_c0[w],
-                  pl->cand_trials + w_tr0[w], n_cand, cs);
+    launch_reduce_partial(d_probs, b, cs);
+    launch_accept(d_probs, b, pl->sc.accept, cs);
+    launch_commit(d_probs, b, pl->sc.accept, trg, d_gptr, d_gpts, pl->cand_ptr + w_c0[w],
+                  pl->cand_trials + w_tr0[w], w_nlist[w], cs);
     launches += 5;
     e = cudaGetLastError();
   }
@@ -1185,9 +1201,111 @@ int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const d
     return fail(DMR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   pl->launches = launches;
-  p->have_partial = false;
+  for (dmr_problem* p : probs) p->have_partial = false;
   *out = pl;
   return DMR_OK;
+}
+
+int check_cands(dmr_problem* p, int n_cand, const int* cand_ids, std::vector<int>& cid) {
+  if (p->n_groups == 0) return fail(DMR_ESTATE, "no FOS registered");
+  if (p->C == 0) return fail(DMR_ESTATE, "no population (call dmr_eval_full first)");
+  if (n_cand < 1 || n_cand > p->C) return fail(DMR_EINVAL, "n_cand out of range");
+  cid.resize(n_cand);
+  CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n_cand, cudaMemcpyDefault));
+  std::vector<int> s(cid);
+  std::sort(s.begin(), s.end());
+  for (int k = 0; k < n_cand; ++k) {
+    if (s[k] < 0 || s[k] >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+    if (k && s[k] == s[k - 1]) return fail(DMR_EINVAL, "duplicate candidate id");
+  }
+  return DMR_OK;
+}
+
+}  // namespace
+
+int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const double* deltas, dmr_plan** out) {
+  if (!p || !cand_ids || !deltas || !out) return fail(DMR_EINVAL, "null argument");
+  *out = nullptr;
+  std::vector<int> cid;
+  int rc = check_cands(p, n_cand, cand_ids, cid);
+  if (rc) return rc;
+  std::vector<std::vector<double>> hd(1, std::vector<double>((size_t)p->n_groups * n_cand * 6 * p->gmax));
+  CU(cudaMemcpy(hd[0].data(), deltas, sizeof(double) * hd[0].size(), cudaMemcpyDefault));
+  return build_plan({p}, p->d_prob, p->d_gptr, p->d_gpts, {0}, {cid}, hd, out);
+}
+
+struct dmr_batch {
+  std::vector<dmr_problem*> probs;
+  DevProblem* d_probs = nullptr;
+  int* d_gptr = nullptr;
+  int* d_gpts = nullptr;
+  std::vector<int> goff;
+};
+
+int dmr_batch_create(int n, dmr_problem* const* probs, dmr_batch** out) {
+  if (!probs || !out || n < 1) return fail(DMR_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  for (int q = 0; q < n; ++q) {
+    if (!probs[q]) return fail(DMR_EINVAL, "null problem in batch");
+    if (probs[q]->storage != probs[0]->storage) return fail(DMR_EINVAL, "problems of a batch share one storage dtype");
+    if (probs[q]->dev != probs[0]->dev) return fail(DMR_EINVAL, "problems of a batch share one device");
+    if (probs[q]->n_groups == 0) return fail(DMR_ESTATE, "every problem of a batch needs a FOS");
+  }
+  dmr_batch* bt = new (std::nothrow) dmr_batch();
+  if (!bt) return fail(DMR_ENOMEM, "host allocation failed");
+  bt->probs.assign(probs, probs + n);
+  std::vector<DevProblem> hp(n);
+  std::vector<int> gptr(1, 0), gpts;
+  for (int q = 0; q < n; ++q) {
+    dmr_problem* p = probs[q];
+    hp[q] = p->hp;
+    bt->goff.push_back((int)gptr.size() - 1);
+    for (int g = 0; g < p->n_groups; ++g) {
+      for (int j = p->g_ptr[g]; j < p->g_ptr[g + 1]; ++j) gpts.push_back(p->g_pts[j]);
+      gptr.push_back((int)gpts.size());
+    }
+  }
+  int rc;
+  if ((rc = dalloc(&bt->d_probs, n)) || (rc = dalloc(&bt->d_gptr, gptr.size())) || (rc = dalloc(&bt->d_gpts, gpts.size()))) {
+    dfree(bt->d_probs);
+    dfree(bt->d_gptr);
+    dfree(bt->d_gpts);
+    delete bt;
+    return rc;
+  }
+  cudaMemcpy(bt->d_probs, hp.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(bt->d_gptr, gptr.data(), sizeof(int) * gptr.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(bt->d_gpts, gpts.data(), sizeof(int) * gpts.size(), cudaMemcpyHostToDevice);
+  *out = bt;
+  return DMR_OK;
+}
+
+int dmr_batch_destroy(dmr_batch* bt) {
+  if (!bt) return DMR_OK;
+  for (dmr_problem* p : bt->probs) cudaStreamSynchronize(p->st);
+  dfree(bt->d_probs);
+  dfree(bt->d_gptr);
+  dfree(bt->d_gpts);
+  delete bt;
+  return DMR_OK;
+}
+
+int dmr_batch_plan_generation(dmr_batch* bt, const int* n_cand, const int* const* cand_ids,
+                              const double* const* deltas, dmr_plan** out) {
+  if (!bt || !n_cand || !cand_ids || !deltas || !out) return fail(DMR_EINVAL, "null argument");
+  *out = nullptr;
+  const int nq = (int)bt->probs.size();
+  std::vector<std::vector<int>> cands(nq);
+  std::vector<std::vector<double>> hd(nq);
+  for (int q = 0; q < nq; ++q) {
+    dmr_problem* p = bt->probs[q];
+    if (!cand_ids[q] || !deltas[q]) return fail(DMR_EINVAL, "null per-problem argument");
+    int rc = check_cands(p, n_cand[q], cand_ids[q], cands[q]);
+    if (rc) return rc;
+    hd[q].resize((size_t)p->n_groups * n_cand[q] * 6 * p->gmax);
+    CU(cudaMemcpy(hd[q].data(), deltas[q], sizeof(double) * hd[q].size(), cudaMemcpyDefault));
+  }
+  return build_plan(bt->probs, bt->d_probs, bt->d_gptr, bt->d_gpts, bt->goff, cands, hd, out);
 }
 
 int dmr_plan_run(dmr_plan* pl) {

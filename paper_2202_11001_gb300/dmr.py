@@ -85,6 +85,9 @@ def load():
         "dmr_set_tile": [vp, i, i],
         "dmr_eval_one_noalloc": [vp, vp, vp],
         "dmr_autotune": [vp, i, ip, ip, ip],
+        "dmr_batch_create": [i, vp, ctypes.POINTER(ctypes.c_void_p)],
+        "dmr_batch_destroy": [vp],
+        "dmr_batch_plan_generation": [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_get_tile": [vp, ip, ip],
     }
     for name, args in sig.items():
@@ -103,7 +106,8 @@ def exported_symbols():
         "dmr_set_fos", "dmr_fos_info", "dmr_fos_waves", "dmr_eval_full", "dmr_eval_partial", "dmr_commit",
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
-        "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_eval_one_noalloc", "dmr_last_error",
+        "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_batch_create", "dmr_batch_destroy",
+        "dmr_batch_plan_generation", "dmr_eval_one_noalloc", "dmr_last_error",
     ]
 
 
@@ -363,6 +367,42 @@ class Problem:
         h = ctypes.c_void_p()
         _check(self._lib.dmr_plan_generation(self.h, len(cand_ids), c.ptr, d.ptr, ctypes.byref(h)))
         return Plan(self, h)
+
+
+class Batch:
+    """Several independent problems served by one set of launches per wave."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        lib = problems[0]._lib
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        h = ctypes.c_void_p()
+        _check(lib.dmr_batch_create(len(self.problems), ctypes.addressof(arr), ctypes.byref(h)))
+        self.h = h
+        self._lib = lib
+
+    def plan_generation(self, cand_ids, deltas):
+        n = len(self.problems)
+        cargs = [_Arg(c, np.int32) for c in cand_ids]
+        dargs = [_Arg(d, np.float64) for d in deltas]
+        nc = (ctypes.c_int * n)(*[len(c) for c in cand_ids])
+        cp = (ctypes.c_void_p * n)(*[a.ptr for a in cargs])
+        dp = (ctypes.c_void_p * n)(*[a.ptr for a in dargs])
+        h = ctypes.c_void_p()
+        _check(self._lib.dmr_batch_plan_generation(self.h, ctypes.addressof(nc), ctypes.addressof(cp),
+                                                   ctypes.addressof(dp), ctypes.byref(h)))
+        return Plan(self.problems[0], h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dmr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

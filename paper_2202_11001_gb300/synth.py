@@ -205,7 +205,7 @@ def ellipsoid_pair(seed=1, n=64, mesh=5, C=128, n_guide=20, amp=None):
         d = rng.normal(size=3)
         d /= np.linalg.norm(d)
         g.append(ctr + ax * d)
-    p = np.array(g)
+    p = np.array(g, dtype=np.float64).reshape(-1, 3)
     q = p.copy()
     for _ in range(8):
         q = p + _disp(q, bumps)

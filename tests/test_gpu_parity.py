@@ -181,3 +181,53 @@ def test_tile_shapes_same_result_and_autotune():
     assert (bw, bv) in table and all(t > 0 for t in table.values())
     assert g.tile() == (bw, bv)
     assert np.array_equal(g.eval_full(pr["coords"]), ref)
+
+
+def _deltas(pr, groups, C, sigma, seed):
+    rng = np.random.default_rng(seed)
+    d = rng.normal(0, sigma, size=(len(groups), C, 2, 3, 1))
+    fix = synth.fixed_axes(pr["mesh"])
+    for gi, grp in enumerate(groups):
+        for ax in range(3):
+            if (fix[grp[0]] >> ax) & 1:
+                d[gi, :, :, ax, 0] = 0.0
+    return d
+
+
+def test_batched_problems_equal_single_plans_and_oracle():
+    """Batching (uneven images, meshes and populations in one launch per
+    kernel and wave) gives exactly the single-problem results."""
+    from paper_2202_11001_gb300 import dmr
+
+    specs = [synth.sphere_pair(seed=20, C=5), synth.ellipsoid_pair(seed=21, n=24, mesh=4, C=7, n_guide=4),
+             synth.sphere_pair(seed=22, n=20, mesh=5, C=3), synth.ellipsoid_pair(seed=23, n=32, mesh=3, C=4, n_guide=0)]
+    for pr in specs:
+        if pr["guide"] is not None and len(pr["guide"]) == 0:
+            pr["guide"] = None
+    single, batched, oracles, plans_in = [], [], [], []
+    for i, pr in enumerate(specs):
+        C = pr["coords"].shape[0]
+        gs, o = make_pair(pr)
+        gb, _ = make_pair(pr)
+        groups = synth.single_point_fos(pr["mesh"])
+        for g in (gs, gb):
+            g.eval_full(pr["coords"])
+            g.set_fos(groups)
+        d = _deltas(pr, groups, C, 0.3 if pr["mesh"][0] <= 3 else 0.8, 30 + i)
+        single.append((gs, gs.plan_generation(np.arange(C, dtype=np.int32), d)))
+        batched.append(gb)
+        plans_in.append((np.arange(C, dtype=np.int32), d))
+        oracles.append(o)
+    bt = dmr.Batch(batched)
+    plan = bt.plan_generation([c for c, _ in plans_in], [d for _, d in plans_in])
+    for _ in range(2):
+        plan.run()
+        for g, pl in single:
+            pl.run()
+    for (gs, _), gb, o, pr in zip(single, batched, oracles, specs):
+        assert np.array_equal(gs.objectives(), gb.objectives())
+        C = pr["coords"].shape[0]
+        final = np.stack([gb.coords(c) for c in range(C)])
+        for c in range(C):
+            assert np.array_equal(final[c], gs.coords(c))
+        assert_obj_close(gb.objectives(), o.eval_full(final))
