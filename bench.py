@@ -70,11 +70,71 @@ def workload(name, seed):
     return pr
 
 
+def run_batch(args):
+    """--workload batch64: 64 independent problems (edge 32..128 voxels, 4..9
+    mesh points per axis, population 64..512) in one graph per generation."""
+    import torch
+
+    from paper_2202_11001_gb300 import dmr, synth
+
+    probs = synth.batch_problems(seed=2)
+    stream = torch.cuda.current_stream().cuda_stream
+    gs, cands, dels = [], [], []
+    for i, pr in enumerate(probs):
+        C = pr["coords"].shape[0]
+        pr["sigma"] = 0.1 * pr["img"][0].shape[0] / (pr["mesh"][0] - 1)
+        g = dmr.Problem(pr["img"][0], pr["img"][1], *pr["spacing"], pr["mesh"], guide=pr["guide"],
+                        model=dmr.LINEAR, storage=args.storage, max_candidates=C, stream=stream)
+        g.eval_full(torch.from_numpy(pr["coords"]).cuda())
+        groups = synth.single_point_fos(pr["mesh"])
+        g.set_fos(groups)
+        gs.append(g)
+        cands.append(np.arange(C, dtype=np.int32))
+        dels.append(deltas_for(pr, groups, C, np.random.default_rng(500 + i)))
+    big = max(range(len(gs)), key=lambda i: probs[i]["coords"].shape[0] * gs[i].ntet)
+    w, v, table = gs[big].autotune()
+    gs[0].set_tile(w, v)
+    bt = dmr.Batch(gs)
+    plan = bt.plan_generation(cands, dels)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        plan.run()
+    torch.cuda.synchronize()
+    for g in gs:
+        g.samples(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, ra = [], 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record()
+        plan.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        ra += plan.kernel_ms()[1]
+    samples = sum(g.samples(reset=True) for g in gs)
+    tot = sum(ms) / 1e3
+    line = {"metric": METRIC, "value": samples / tot, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+            "data": "synthetic (64 seeded ellipsoid problems)",
+            "config": {"workload": "batch64: 64 problems, edge U{32..128}, mesh U{4..9}^3 points, population "
+                                   "U{64..512}, one persistent launch per kernel and wave, one graph per generation",
+                       "storage": args.storage, "problems": len(gs), "tile": [w, v],
+                       "samples_per_step": samples / args.steps,
+                       "raster_ms_per_step": ra / args.steps},
+            "gpu_launches": plan.launches * args.steps}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    bt.close()
+    return 0
+
+
 def deltas_for(pr, groups, C, rng):
     from paper_2202_11001_gb300 import synth
 
     fix = synth.fixed_axes(pr["mesh"])
-    d = rng.normal(0.0, pr["sigma"], size=(len(groups), C, 2, 3, 1))
+    d = rng.normal(0.0, pr.get("sigma", 1.0), size=(len(groups), C, 2, 3, 1))
     for gi, grp in enumerate(groups):
         for ax in range(3):
             if (fix[grp[0]] >> ax) & 1:
@@ -245,6 +305,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
 
     import torch
 
