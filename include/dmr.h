@@ -222,6 +222,42 @@ int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, flo
  * enqueued on the problem's stream; the call does not wait for it. */
 int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double* obj_out);
 
+/* Exact hypervolume (host code, no GPU): the measure of the union of the
+ * boxes [p_i, ref] of n points of dimension d (1..6, minimisation), the
+ * quality score of an approximation set (Sec. 1; the elitist archive of
+ * Sec. 2.4).  pts [n][d] and ref [d] host; points not strictly below ref in
+ * every coordinate add nothing.  *out receives the volume. */
+int dmr_hypervolume(const double* pts, int n, int d, const double* ref, double* out);
+
+/* Learned proposal (a network the paper does not have; the method's own
+ * proposals stay the judge: every proposal is still scored by the
+ * evaluator).  An MLP 256 -> 128 -> 128 -> 128 -> 6 with GELU maps features
+ * of a (candidate, point) -- 5x5x5 trilinear patches of both images around
+ * the source and target point, the correspondence offset and the position --
+ * to the mean (3) and log-variance (3) of a Gaussian displacement of the
+ * target-mesh point.  BF16 weights and activations, FP32 accumulation on the
+ * tensor cores (tcgen05.mma, TMEM accumulators); FP32 master weights and Adam.
+ * Parameters are FP32 [W1 (128x256), b1, W2 (128x128), b2, W3, b3,
+ * W4 (16x128; rows 6..15 zero), b4 (16)], weights [out][in]. */
+typedef struct dmr_mlp dmr_mlp;
+int dmr_mlp_create(unsigned long long seed, void* stream, dmr_mlp** out);
+int dmr_mlp_destroy(dmr_mlp* mlp);
+int dmr_mlp_n_params(void);
+/* Copy parameters out to `get` and/or in from `set` (host or device, FP32
+ * [n_params]); either may be NULL.  Setting resets the Adam state. */
+int dmr_mlp_params(dmr_mlp* mlp, float* get, const float* set);
+/* Features of every (candidate, point) of coords (device [C][2][3][P]) into
+ * X (device BF16 [C*P][256]). */
+int dmr_mlp_features(dmr_problem* p, const double* coords, int C, void* X);
+/* out (device FP32 [n][6]) = network(X) for X device BF16 [n][256]. */
+int dmr_mlp_forward(dmr_mlp* mlp, const void* X, int n, float* out);
+/* Gaussian negative log-likelihood of targets Y (device FP32 [n][3]) on
+ * batch X; gradient by backpropagation on the tensor cores; if lr > 0 one
+ * Adam step.  loss_out (host, may be NULL) = mean loss before the step;
+ * grad_out (host FP32 [n_params], may be NULL) = the gradient. */
+int dmr_mlp_train_step(dmr_mlp* mlp, const void* X, const float* Y, int n, float lr, float* loss_out,
+                       float* grad_out);
+
 const char* dmr_last_error(void);
 
 #ifdef __cplusplus

@@ -280,3 +280,20 @@ class Oracle:
 
     def six_vol(self, mesh, coords1, t):
         return float(self._lib.dmo_six_vol(self.h, int(mesh), _f64(coords1).reshape(-1), int(t)))
+
+
+def hypervolume_bruteforce(points, ref):
+    """Hypervolume as the plain definition: the measure of the union of the
+    boxes [p_i, ref], by inclusion-exclusion over all non-empty subsets (the
+    intersection of boxes [p_i, ref] is the box [max_i p_i, ref]).  Small n
+    only (2^n subsets)."""
+    import itertools
+
+    pts = [np.asarray(p, np.float64) for p in points if np.all(np.asarray(p) < np.asarray(ref))]
+    ref = np.asarray(ref, np.float64)
+    total = 0.0
+    for k in range(1, len(pts) + 1):
+        for sub in itertools.combinations(pts, k):
+            corner = np.max(np.stack(sub), axis=0)
+            total += (-1) ** (k + 1) * float(np.prod(ref - corner))
+    return total

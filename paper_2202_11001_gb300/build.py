@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmr.so")
 SOURCES = ["dmr_api.cu", "dmr_kernels.cu", "dmr_noalloc.cu", "dmr_raster_f32.cu", "dmr_raster_bf16.cu",
-           "dmr_raster_f16.cu"]
+           "dmr_raster_f16.cu", "dmr_hv.cpp", "dmr_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -47,7 +47,7 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_v: bool = Fa
         common += ["-DDMR_RASTER_THREADS_PER_SM=%d" % int(os.environ["DMR_RASTER_THREADS_PER_SM"])]
     procs, objs = [], []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         objs.append(obj)
         cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:

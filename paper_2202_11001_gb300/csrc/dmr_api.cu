@@ -323,6 +323,8 @@ int problem_view(const ::dmr_problem* p, DevProblem* hp, int* storage, int* warp
   return DMR_OK;
 }
 
+const DevProblem* problem_device(const ::dmr_problem* p) { return p ? p->d_prob : nullptr; }
+
 }  // namespace dmr
 
 extern "C" {

@@ -136,5 +136,7 @@ void launch_propose(const DevProblem* probs, const Batch& b, const int* tr_group
 int set_error(int code, const std::string& msg);
 // Host copy of a problem's device descriptor plus its launch settings.
 int problem_view(const ::dmr_problem* p, DevProblem* hp, int* storage, int* warps, int* n_sm, cudaStream_t* st);
+// The problem's device descriptor (an array of one).
+const DevProblem* problem_device(const ::dmr_problem* p);
 
 }  // namespace dmr

@@ -88,6 +88,14 @@ def load():
         "dmr_batch_create": [i, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_batch_destroy": [vp],
         "dmr_batch_plan_generation": [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_void_p)],
+        "dmr_hypervolume": [vp, i, i, vp, vp],
+        "dmr_mlp_create": [ctypes.c_ulonglong, vp, ctypes.POINTER(ctypes.c_void_p)],
+        "dmr_mlp_destroy": [vp],
+        "dmr_mlp_n_params": [],
+        "dmr_mlp_params": [vp, vp, vp],
+        "dmr_mlp_features": [vp, vp, i, vp],
+        "dmr_mlp_forward": [vp, vp, i, vp],
+        "dmr_mlp_train_step": [vp, vp, vp, i, ctypes.c_float, vp, vp],
         "dmr_get_tile": [vp, ip, ip],
     }
     for name, args in sig.items():
@@ -107,7 +115,8 @@ def exported_symbols():
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
         "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_batch_create", "dmr_batch_destroy",
-        "dmr_batch_plan_generation", "dmr_eval_one_noalloc", "dmr_last_error",
+        "dmr_batch_plan_generation", "dmr_hypervolume", "dmr_mlp_create", "dmr_mlp_destroy", "dmr_mlp_n_params",
+        "dmr_mlp_params", "dmr_mlp_features", "dmr_mlp_forward", "dmr_mlp_train_step", "dmr_eval_one_noalloc", "dmr_last_error",
     ]
 
 
@@ -169,6 +178,17 @@ def _out_like(ref, shape, dtype):
 
 def _addr(buf):
     return buf.data_ptr() if _is_torch(buf) else buf.ctypes.data
+
+
+def hypervolume(points, ref):
+    """Exact hypervolume of ``points`` [n, d] (minimisation) w.r.t. ``ref``."""
+    lib = load()
+    pts = np.ascontiguousarray(np.asarray(points, np.float64).reshape(-1, len(ref)))
+    r = np.ascontiguousarray(np.asarray(ref, np.float64))
+    out = ctypes.c_double()
+    _check(lib.dmr_hypervolume(pts.ctypes.data if len(pts) else None, len(pts), len(r), r.ctypes.data,
+                               ctypes.addressof(out)))
+    return out.value
 
 
 class Problem:
@@ -427,6 +447,65 @@ class Plan:
     def close(self):
         if getattr(self, "h", None):
             self.prob._lib.dmr_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The learned-proposal network; tensors are torch CUDA tensors."""
+
+    def __init__(self, seed=0, stream=None):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.dmr_mlp_create(int(seed), stream, ctypes.byref(h)))
+        self.h = h
+        self.n_params = self._lib.dmr_mlp_n_params()
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(self._lib.dmr_mlp_params(self.h, out.ctypes.data, None))
+        return out
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, np.float32)
+        assert a.size == self.n_params
+        _check(self._lib.dmr_mlp_params(self.h, None, a.ctypes.data))
+
+    @staticmethod
+    def features(prob, coords):
+        """coords: torch CUDA float64 [C, 2, 3, P] -> BF16 (as int16) [C*P, 256]."""
+        import torch
+
+        C = coords.shape[0]
+        X = torch.empty((C * prob.P, 256), dtype=torch.bfloat16, device=coords.device)
+        c = coords.contiguous()
+        _check(load().dmr_mlp_features(prob.h, c.data_ptr(), C, X.data_ptr()))
+        return X
+
+    def forward(self, X):
+        import torch
+
+        out = torch.empty((X.shape[0], 6), dtype=torch.float32, device=X.device)
+        Xc = X.contiguous()
+        _check(self._lib.dmr_mlp_forward(self.h, Xc.data_ptr(), X.shape[0], out.data_ptr()))
+        return out
+
+    def train_step(self, X, Y, lr, want_grad=False):
+        Xc, Yc = X.contiguous(), Y.contiguous().float()
+        loss = ctypes.c_float()
+        g = np.zeros(self.n_params, np.float32) if want_grad else None
+        _check(self._lib.dmr_mlp_train_step(self.h, Xc.data_ptr(), Yc.data_ptr(), X.shape[0], float(lr),
+                                            ctypes.addressof(loss), g.ctypes.data if g is not None else None))
+        return (loss.value, g) if want_grad else loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dmr_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

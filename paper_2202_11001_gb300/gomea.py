@@ -1,0 +1,149 @@
+"""Minimal multi-objective GOMEA scaffold over the C-ABI evaluator.
+
+Only what measuring "hypervolume at a fixed evaluation budget" needs; the
+paper specifies the optimiser only as far as Sec. 2.2 (FOS groups changed
+together, a change accepted only if it improves, independent groups changed
+in parallel) and Sec. 2.4 (approximation set from an elitist archive of
+non-dominated solutions).  Per generation and wave of independent groups:
+sample a proposal for every (candidate, group), evaluate partially on the
+GPU, accept-if-improves and commit on the GPU.  Proposal = current group
+coordinates + N(0, s_g^2) on the free axes of both meshes, s_g adapted per
+group with the 1/5 success rule; optionally (learned proposal) the
+target-mesh part of a trial is drawn from the MLP's Gaussian instead, with
+probability alpha.
+
+Budget (GOMEA convention): a partial evaluation costs |touched tets| / N_tet
+of a full evaluation; a full evaluation costs 1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dmr, synth
+
+
+def nondominated(objs):
+    """Mask of the rows of ``objs`` [n, d] not dominated by another row."""
+    n = len(objs)
+    keep = np.ones(n, bool)
+    for i in range(n):
+        if not keep[i]:
+            continue
+        dom = np.all(objs <= objs[i], axis=1) & np.any(objs < objs[i], axis=1)
+        if dom.any():
+            keep[i] = False
+    return keep
+
+
+class Archive:
+    """Elitist archive: feasible, mutually non-dominated (f_sim, f_def, f_guid)."""
+
+    def __init__(self, cap=2000):
+        self.cap = cap
+        self.objs = np.zeros((0, 3))
+        self.coords = []
+
+    def update(self, objs, coords_of):
+        new_o, new_c = [], []
+        for c in np.nonzero(objs[:, 3] == 0)[0]:
+            o = objs[c, :3]
+            if any(np.array_equal(o, x) for x in self.objs) or any(np.array_equal(o, x) for x in new_o):
+                continue
+            new_o.append(o)
+            new_c.append(int(c))
+        if not new_o:
+            return
+        n_old = len(self.objs)
+        allo = np.vstack([self.objs, np.array(new_o)])
+        keep = nondominated(allo)
+        coords = list(self.coords) + [None] * len(new_o)
+        for j, c in enumerate(new_c):
+            if keep[n_old + j]:
+                coords[n_old + j] = coords_of(c)
+        self.objs = allo[keep]
+        self.coords = [coords[i] for i in np.nonzero(keep)[0]]
+        if len(self.objs) > self.cap:
+            idx = np.random.default_rng(0).choice(len(self.objs), self.cap, replace=False)
+            self.objs = self.objs[idx]
+            self.coords = [self.coords[i] for i in idx]
+
+    def hypervolume(self, ref):
+        return dmr.hypervolume(self.objs, ref) if len(self.objs) else 0.0
+
+
+class Gomea:
+    def __init__(self, prob, coords0, groups, mesh, sigma0, rng, proposal=None, alpha=0.25):
+        self.prob = prob
+        self.mesh = mesh
+        self.groups = groups
+        self.rng = rng
+        self.C = coords0.shape[0]
+        self.coords = np.array(coords0, np.float64)
+        self.obj = np.asarray(prob.eval_full(self.coords))
+        prob.set_fos(groups)
+        self.waves = prob.waves()
+        self.sigma = np.full(len(groups), float(sigma0))
+        self.fix = synth.fixed_axes(mesh)
+        self.evals = float(self.C)
+        self.ntet = prob.ntet
+        self.touched = self._touched_counts()
+        self.archive = Archive()
+        self.archive.update(self.obj, lambda c: self.coords[c].copy())
+        self.proposal = proposal  # callable(coords [C,2,3,P]) -> (mean [C,P,3], logvar [C,P,3]) or None
+        self.alpha = alpha
+        self.history = [(self.evals, None)]
+
+    def _touched_counts(self):
+        """|union of the stars of the group's points| per group."""
+        tets = self.prob.tets()
+        flat = tets.reshape(-1)
+        tet_of = np.repeat(np.arange(len(tets)), 4)
+        order = np.argsort(flat, kind="stable")
+        starts = np.searchsorted(flat[order], np.arange(self.prob.P + 1))
+        out = []
+        for grp in self.groups:
+            parts = [tet_of[order[starts[p]:starts[p + 1]]] for p in grp]
+            out.append(len(np.unique(np.concatenate(parts))))
+        return np.array(out, np.float64)
+
+    def generation(self):
+        learned = None
+        if self.proposal is not None:
+            learned = self.proposal(self.coords)
+        G = max(len(g) for g in self.groups)
+        succ = np.zeros(len(self.groups))
+        tries = np.zeros(len(self.groups))
+        for w in self.waves:
+            cids = np.repeat(np.arange(self.C), len(w)).astype(np.int32)
+            gids = np.tile(w, self.C).astype(np.int32)
+            tc = np.zeros((len(gids), 2, 3, G))
+            for k, (g, c) in enumerate(zip(gids, cids)):
+                pts = self.groups[g]
+                cur = self.coords[c][:, :, pts]
+                noise = self.rng.normal(0.0, self.sigma[g], size=cur.shape)
+                if learned is not None and self.rng.uniform() < self.alpha:
+                    mu, lv = learned[0][c][pts].T, learned[1][c][pts].T  # [3, n]
+                    noise[1] = mu + np.exp(0.5 * lv) * self.rng.normal(size=mu.shape)
+                for ax in range(3):
+                    noise[:, ax, ((self.fix[pts] >> ax) & 1) == 1] = 0.0
+                tc[k, :, :, : len(pts)] = cur + noise
+            self.prob.eval_partial(gids, cids, tc)
+            acc = self.prob.commit_improving()
+            for k in np.nonzero(acc)[0]:
+                g, c = gids[k], cids[k]
+                self.coords[c][:, :, self.groups[g]] = tc[k, :, :, : len(self.groups[g])]
+            np.add.at(succ, gids, acc)
+            np.add.at(tries, gids, 1)
+            self.evals += float(np.sum(self.touched[gids])) / self.ntet
+        rate = succ / np.maximum(tries, 1)
+        self.sigma *= np.where(rate > 0.2, 1.2, 0.85)
+        self.obj = self.prob.objectives()
+        self.archive.update(self.obj, lambda c: self.coords[c].copy())
+        return self.obj
+
+    def run(self, generations, ref):
+        hv = []
+        for _ in range(generations):
+            self.generation()
+            hv.append((self.evals, self.archive.hypervolume(ref)))
+        return hv
