@@ -130,6 +130,64 @@ def run_batch(args):
     return 0
 
 
+def run_learned(args):
+    """--workload learned: the learned proposal on the coarse CT level (64x64x24,
+    10^3-point meshes, population 512): collect elites from plain runs, train
+    the network on the tensor cores, then compare hypervolume against
+    evaluations with and without the learned sampler.  Also times the fused
+    network forward over one generation's 512 x 1000 rows."""
+    import torch
+
+    from paper_2202_11001_gb300 import dmr, learned, synth
+
+    pr = synth.ct_phantom(seed=3, C=512, level="coarse")
+    rng = np.random.default_rng(0)
+    t0 = time.time()
+    X, Y = learned.collect(pr, seeds=[11, 12], generations=args.steps, sigma0=0.5, n_samples=100000, rng=rng)
+    t_collect = time.time() - t0
+    net = dmr.MLP(seed=1)
+    t0 = time.time()
+    losses = learned.train(net, X, Y, steps=600, batch=4096, lr=1e-3, rng=rng)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    # inference throughput: features + fused forward for 512 x 1000 rows
+    prob = learned.make_problem(pr)
+    coords = torch.from_numpy(pr["coords"]).cuda()
+    Xi = dmr.MLP.features(prob, coords)
+    for _ in range(3):
+        net.forward(Xi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 10
+    for _ in range(reps):
+        net.forward(Xi)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    rows = Xi.shape[0]
+    flop = rows * 2.0 * (256 * 128 + 128 * 128 * 2 + 128 * 16)
+    peaks, kind = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0)) if kind == "measured" else 1900.0
+    ref, cmp_rows = learned.compare(pr, net, seeds=[21, 22, 23], generations=args.steps, sigma0=0.5, alpha=0.25)
+    pe = [r["plain_evals"] for r in cmp_rows]
+    le = [r["learned_evals"] for r in cmp_rows]
+    line = {"metric": "HV at fixed eval budget", "workload": "ct64 coarse level (64x64x24, 4x4x12 mm), 10^3-point "
+            "meshes, population 512, 1000 single-point groups, learned sampler alpha 0.25",
+            "generations": args.steps, "reference_point": ref.tolist(),
+            "per_seed": [{k: v for k, v in r.items() if k != "curves"} for r in cmp_rows],
+            "evals_to_plain_final_hv": {"plain": pe, "learned": le},
+            "train": {"samples": int(X.shape[0]), "steps": 600, "batch": 4096, "loss_first": losses[0],
+                      "loss_last": losses[-1], "seconds": t_train, "collect_seconds": t_collect},
+            "forward": {"rows": rows, "ms": fwd_ms, "tflops": flop / fwd_ms / 1e9,
+                        "roofline": {"bound": "tensor", "achieved": flop / fwd_ms / 1e9, "peak": peak,
+                                     "unit": "TFLOP/s", "frac": flop / fwd_ms / 1e9 / peak,
+                                     "peak_kind": kind}},
+            "curves": {str(r["seed"]): {a: r["curves"][a] for a in ("plain", "learned")} for r in cmp_rows}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def deltas_for(pr, groups, C, rng):
     from paper_2202_11001_gb300 import synth
 
@@ -307,6 +365,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "learned":
+        return run_learned(args)
 
     import torch
 

@@ -106,32 +106,53 @@ class Gomea:
             out.append(len(np.unique(np.concatenate(parts))))
         return np.array(out, np.float64)
 
-    def generation(self):
-        learned = None
-        if self.proposal is not None:
-            learned = self.proposal(self.coords)
+    def _proposals(self, gids, cids, learned):
+        """Trial coordinates [n, 2, 3, G] for (group, candidate) pairs."""
         G = max(len(g) for g in self.groups)
+        n = len(gids)
+        if G == 1:  # single-point groups: vectorised
+            pts = np.array([self.groups[g][0] for g in gids])
+            cur = self.coords[cids, :, :, pts]  # [n, 2, 3]
+            noise = self.rng.normal(0.0, 1.0, size=cur.shape) * self.sigma[gids][:, None, None]
+            if learned is not None:
+                use = self.rng.uniform(size=n) < self.alpha
+                mu = learned[0][cids, pts]          # [n, 3]
+                lv = learned[1][cids, pts]
+                lt = mu + np.exp(0.5 * lv) * self.rng.normal(size=mu.shape)
+                noise[use, 1, :] = lt[use]
+            fixed = ((self.fix[pts][:, None] >> np.arange(3)[None, :]) & 1) == 1  # [n, 3]
+            noise[np.repeat(fixed[:, None, :], 2, axis=1)] = 0.0
+            return (cur + noise)[..., None]
+        tc = np.zeros((n, 2, 3, G))
+        for k, (g, c) in enumerate(zip(gids, cids)):
+            pts = self.groups[g]
+            cur = self.coords[c][:, :, pts]
+            noise = self.rng.normal(0.0, self.sigma[g], size=cur.shape)
+            if learned is not None and self.rng.uniform() < self.alpha:
+                noise[1] = learned[0][c][pts].T + np.exp(0.5 * learned[1][c][pts].T) * self.rng.normal(size=(3, len(pts)))
+            for ax in range(3):
+                noise[:, ax, ((self.fix[pts] >> ax) & 1) == 1] = 0.0
+            tc[k, :, :, : len(pts)] = cur + noise
+        return tc
+
+    def generation(self):
+        learned = self.proposal(self.coords) if self.proposal is not None else None
         succ = np.zeros(len(self.groups))
         tries = np.zeros(len(self.groups))
         for w in self.waves:
             cids = np.repeat(np.arange(self.C), len(w)).astype(np.int32)
             gids = np.tile(w, self.C).astype(np.int32)
-            tc = np.zeros((len(gids), 2, 3, G))
-            for k, (g, c) in enumerate(zip(gids, cids)):
-                pts = self.groups[g]
-                cur = self.coords[c][:, :, pts]
-                noise = self.rng.normal(0.0, self.sigma[g], size=cur.shape)
-                if learned is not None and self.rng.uniform() < self.alpha:
-                    mu, lv = learned[0][c][pts].T, learned[1][c][pts].T  # [3, n]
-                    noise[1] = mu + np.exp(0.5 * lv) * self.rng.normal(size=mu.shape)
-                for ax in range(3):
-                    noise[:, ax, ((self.fix[pts] >> ax) & 1) == 1] = 0.0
-                tc[k, :, :, : len(pts)] = cur + noise
+            tc = self._proposals(gids, cids, learned)
             self.prob.eval_partial(gids, cids, tc)
             acc = self.prob.commit_improving()
-            for k in np.nonzero(acc)[0]:
-                g, c = gids[k], cids[k]
-                self.coords[c][:, :, self.groups[g]] = tc[k, :, :, : len(self.groups[g])]
+            ks = np.nonzero(acc)[0]
+            if tc.shape[-1] == 1:
+                pts = np.array([self.groups[g][0] for g in gids[ks]], dtype=np.int64)
+                self.coords[cids[ks], :, :, pts] = tc[ks, :, :, 0]
+            else:
+                for k in ks:
+                    g, c = gids[k], cids[k]
+                    self.coords[c][:, :, self.groups[g]] = tc[k, :, :, : len(self.groups[g])]
             np.add.at(succ, gids, acc)
             np.add.at(tries, gids, 1)
             self.evals += float(np.sum(self.touched[gids])) / self.ntet
