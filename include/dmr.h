@@ -214,7 +214,7 @@ int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, flo
  * device [4] FP64, the same four values dmr_eval_full gives.  Limits:
  * N_tet <= 4608 and n_guide <= 512, else DMR_EINVAL.  The problem's images,
  * topology and population state are only read; the scratch is one fixed
- * array of about 5.6 MB that every device holds from the first call until
+ * array of about 6.3 MB that every device holds from the first call until
  * the process exits.  The first call on a device looks that array up
  * (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls share the array: calls that may overlap on the GPU (other streams,

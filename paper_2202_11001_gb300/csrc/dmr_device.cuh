@@ -64,13 +64,30 @@ static __device__ __forceinline__ bool rec_face_in_exact(const ItemRec& r, uint3
 }
 
 // FP64 mapped coordinate, the definition the black decision follows:
-// p' = (v + d0) + G (v - own_0).
+// p' = (v + d0) + G (v - own_0) with G = [D1 D2 D3][r1; r2; r3] / det
+// (Sec. 2.3.1), every operation in the oracle's order, rebuilt from the own
+// and partner vertices of the record (only decisions the FP32 path cannot
+// certify come here).
 static __device__ __noinline__ void map_exact(const ItemRec& r, const double v[3], double out[3]) {
+  double e[3][3], D[3][3], rr[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a) {
+      e[i][a] = dsub(r.X[i + 1][a], r.X[0][a]);
+      D[i][a] = dsub(dsub(r.XP[i + 1][a], r.XP[0][a]), e[i][a]);
+    }
+  cross3d(e[1], e[2], rr[0]);
+  cross3d(e[2], e[0], rr[1]);
+  cross3d(e[0], e[1], rr[2]);
+  const double inv = 1.0 / dot3d(e[0], rr[0]);
   double q[3];
   for (int a = 0; a < 3; ++a) q[a] = dsub(v[a], r.X[0][a]);
-  for (int c = 0; c < 3; ++c)
-    out[c] = dadd(dadd(v[c], r.d0[c]),
-                  dadd(dmul(r.G64[c][0], q[0]), dadd(dmul(r.G64[c][1], q[1]), dmul(r.G64[c][2], q[2]))));
+  for (int c = 0; c < 3; ++c) {
+    double G[3];
+    for (int j = 0; j < 3; ++j)
+      G[j] = dmul(dadd(dmul(D[0][c], rr[0][j]), dadd(dmul(D[1][c], rr[1][j]), dmul(D[2][c], rr[2][j]))), inv);
+    out[c] = dadd(dadd(v[c], dsub(r.XP[0][c], r.X[0][c])),
+                  dadd(dmul(G[0], q[0]), dadd(dmul(G[1], q[1]), dmul(G[2], q[2]))));
+  }
 }
 
 // ------------------------------------------------------------ float helpers
@@ -168,35 +185,57 @@ static __device__ __forceinline__ void slice_yrange(const ItemRec& r, float zr, 
     }
 }
 
-// Exact span of row (y, z): x range (relative to O) inside all 4 faces.
-// Returns false when the row is empty.  Rows where the FP32 margin cannot
-// decide a face take the careful path: every voxel of the row range is
-// classified face by face, exactly where the margin does not decide.
+// Exact span of row (y, z): x range (relative to O) inside all 4 faces, for
+// rows where the FP32 margins cannot certify the fast span.  For a fixed row
+// the FP64 face predicate is monotone in x (every rounding step is), with
+// direction sign(s n_x), and the tie rule is constant per face; so each
+// face's inside set is a prefix or suffix of the row, and the row's span is
+// an interval.  Where |A.x| exceeds the bound on its rounding error (fm[3])
+// the direction is sign(A.x): walk from the FP32 threshold to the exact
+// boundary, deciding each voxel with the margin and, inside it, with the
+// FP64 predicate.  Otherwise scan the row for that face.
 static __device__ __noinline__ void span_careful(const ItemRec& r, uint32_t fp, int xl, int xh, int yi, int zi,
-                                          int& lo, int& hi) {
+                                                 int& lo, int& hi) {
   const float yr = (float)yi, zr = (float)zi;
-  int first = xh + 1, last = xl - 1;
-  for (int x = xl; x <= xh; ++x) {
-    bool in = true;
-    for (int f = 0; f < 4 && in; ++f) {
-      float c = fmaf(r.fa[f][1], yr, fmaf(r.fa[f][2], zr, r.fa[f][3]));
-      float h = fmaf(r.fa[f][0], (float)x, c);
-      float mu = r.fm[f][0];
-      if (h > mu) continue;
-      if (h < -mu) {
-        in = false;
-        break;
+  const double py = (double)(yi + r.O[1]), pz = (double)(zi + r.O[2]);
+  lo = xl;
+  hi = xh;
+  for (int f = 0; f < 4 && lo <= hi; ++f) {
+    const float Ax = r.fa[f][0];
+    const float c = fmaf(r.fa[f][1], yr, fmaf(r.fa[f][2], zr, r.fa[f][3]));
+    const float mu = r.fm[f][0];
+    auto in_f = [&](int x) -> bool {
+      const float h = fmaf(Ax, (float)x, c);
+      if (h > mu) return true;
+      if (h < -mu) return false;
+      const double p[3] = {(double)(x + r.O[0]), py, pz};
+      return rec_face_in_exact(r, fp, f, p);
+    };
+    if (fabsf(Ax) > r.fm[f][3]) {
+      const float th = fminf(fmaxf(-c * r.fm[f][1], (float)(lo - 1)), (float)(hi + 1));
+      const int k = (int)floorf(th);
+      if (Ax > 0.f) {
+        int xs = min(max(k + 1, lo), hi + 1);
+        while (xs > lo && in_f(xs - 1)) --xs;
+        while (xs <= hi && !in_f(xs)) ++xs;
+        lo = xs;
+      } else {
+        int xe = min(max(k, lo - 1), hi);
+        while (xe < hi && in_f(xe + 1)) ++xe;
+        while (xe >= lo && !in_f(xe)) --xe;
+        hi = xe;
       }
-      double p[3] = {(double)(x + r.O[0]), (double)(yi + r.O[1]), (double)(zi + r.O[2])};
-      in = rec_face_in_exact(r, fp, f, p);
-    }
-    if (in) {
-      first = min(first, x);
-      last = max(last, x);
+    } else {
+      int first = hi + 1, last = lo - 1;
+      for (int x = lo; x <= hi; ++x)
+        if (in_f(x)) {
+          first = min(first, x);
+          last = x;
+        }
+      lo = first;
+      hi = last;
     }
   }
-  lo = first;
-  hi = last;
 }
 
 // Exact span of row (y, z), x relative to O.  Every face's FP32 threshold
@@ -444,7 +483,18 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
           // coordinates cannot leave [-1, n], so the clamps are skipped
           const bool inside = (r.flags & 2) != 0;
           int rows_before = 0;
+          // plain FP32 partial sum over at most 256 voxels of the batch (<= 8
+          // samples per lane), folded into the Kahan pair afterwards; the
+          // fold points do not depend on the tile shape
+          float bsum = 0.f;
           for (int vb = 0; vb < T; vb += 32 * VPL) {
+            if (vb != 0 && (vb & 255) == 0) {
+              const float yk = bsum - comp;
+              const float tk = sum + yk;
+              comp = (tk - sum) - yk;
+              sum = tk;
+              bsum = 0.f;
+            }
             int row[VPL], vv[VPL];
 #pragma unroll
             for (int u = 0; u < VPL; ++u) {
@@ -513,13 +563,16 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
                   }
                   if ((o == 0.0f) != blk) d2 = 1.0f;
                 }
-                const float yk = d2 - comp;
-                const float tk = sum + yk;
-                comp = (tk - sum) - yk;
-                sum = tk;
+                bsum += d2;
                 ++cov;
               }
             }
+          }
+          {
+            const float yk = bsum - comp;
+            const float tk = sum + yk;
+            comp = (tk - sum) - yk;
+            sum = tk;
           }
           __syncwarp();
         }

@@ -71,14 +71,15 @@ struct __align__(16) ItemRec {
   int pad0[3];
   float vr[4][4];   // own vertices relative to O (x,y,z,-)
   float fa[4][4];   // face f: inward normal A (x,y,z), offset B'
-  float fm[4][4];   // face f: margin mu, 1/A.x, -, -
+  float fm[4][4];   // face f: margin mu (box points), 1/A.x, margin growth per voxel of |p - O|,
+                    // bound on the rounding error of A.x
   float G[3][4];    // map matrix rows (FP32), col 3 = k (offset)
   float gx[4];      // (1+G00, G10, G20, delta)
   float clo[4];     // clamp range of partner-relative mapped coords
   float chi[4];
   double X[4][3];   // own vertices FP64 (abs)
-  double G64[3][3]; // FP64 map matrix
-  double d0[3];     // partner_0 - own_0
+  double XP[4][3];  // partner vertices FP64 (abs): the exact map is rebuilt from them
+  double Gd[3][3];  // FP64 map matrix (fused multiply-adds, a few ulps from the exact order)
 };
 
 // A batch of (trial, tet) pairs to evaluate.

@@ -105,6 +105,21 @@ __device__ __forceinline__ double vcoord(const DevProblem& pr, const Batch& b, i
 
 __device__ __forceinline__ float fabs3max(float a, float b, float c) { return fmaxf(fabsf(a), fmaxf(fabsf(b), fabsf(c))); }
 
+// Edge vector X_j - X_i (i != j, local ids) from the six edges
+// E6 = {01, 02, 03, 12, 13, 23} (x - y = -(y - x) exactly), without
+// indexing local memory.
+__device__ __forceinline__ double edge6(const double (&E)[6][3], int i, int j, int a) {
+  const int lo = min(i, j), hi = max(i, j);
+  const int k = lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5);
+  const double v = k == 0 ? E[0][a] : k == 1 ? E[1][a] : k == 2 ? E[2][a] : k == 3 ? E[3][a] : k == 4 ? E[4][a] : E[5][a];
+  return i < j ? v : -v;
+}
+
+// v[i][a] for a runtime vertex index i without indexing local memory
+__device__ __forceinline__ float pick4(const float (&v)[4][3], int i, int a) {
+  return i == 0 ? v[0][a] : i == 1 ? v[1][a] : i == 2 ? v[2][a] : v[3][a];
+}
+
 // One thread per (trial, tet): fold count, deformation, and the two
 // direction records (Sec. 2.3.1-2.3.4).
 __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b) {
@@ -124,42 +139,52 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
     for (int i = 0; i < 4; ++i)
       for (int a = 0; a < 3; ++a) X[mesh][i][a] = vcoord(pr, b, k, cand, slots, i, vid[i], mesh, a);
 
-  // edge vectors, differences, fold (FP64, oracle expression order)
+  // edge vectors and fold (FP64, oracle expression order: the volume sign
+  // decides an integer)
   double e[2][3][3];
   for (int mesh = 0; mesh < 2; ++mesh)
     for (int i = 0; i < 3; ++i)
       for (int a = 0; a < 3; ++a) e[mesh][i][a] = dsub(X[mesh][i + 1][a], X[mesh][0][a]);
   int fold = 0;
-  double vol6[2];
+  double vol6[2], r0[2][3];
   for (int mesh = 0; mesh < 2; ++mesh) {
-    double r1[3];
-    cross3d(e[mesh][1], e[mesh][2], r1);
-    vol6[mesh] = dot3d(e[mesh][0], r1);
+    cross3d(e[mesh][1], e[mesh][2], r0[mesh]);
+    vol6[mesh] = dot3d(e[mesh][0], r0[mesh]);
     if (!(vol6[mesh] > 0 && isfinite(vol6[mesh]))) ++fold;
   }
+  // fixed axes: the coordinate must equal its border value exactly; both
+  // sides are never 0, so equality is equality of the bit patterns (a NaN
+  // differs from every border value either way)
   for (int i = 0; i < 4; ++i) {
     uint8_t fm = pr.fixmask[vid[i]];
+    if (!fm) continue;
     for (int mesh = 0; mesh < 2; ++mesh) {
       int bad = 0;
       for (int a = 0; a < 3; ++a)
         if ((fm >> a) & 1) {
           double rv = ((fm >> (3 + a)) & 1) ? (double)pr.n[mesh][a] - 0.5 : -0.5;
-          if (!(X[mesh][i][a] == rv)) bad = 1;
+          if (__double_as_longlong(X[mesh][i][a]) != __double_as_longlong(rv)) bad = 1;
         }
       fold += bad;
     }
   }
   b.o_fold[tt] = fold;
 
-  // deformation (FP32 from FP64 edge vectors and their differences)
-  float es[3][3], dd[3][3];
+  // edge differences target - source (direction 0's D; direction 1 uses -D,
+  // exactly, since a - b = -(b - a) in round-to-nearest)
+  double Dm[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int a = 0; a < 3; ++a) {
-      es[i][a] = (float)e[0][i][a];
-      dd[i][a] = (float)dsub(e[1][i][a], e[0][i][a]);
-    }
+    for (int a = 0; a < 3; ++a) Dm[i][a] = dsub(e[1][i][a], e[0][i][a]);
+
+  // deformation (FP32 from FP64 edge vectors and their differences)
   double def = 0.0;
   if (pr.model == 0) {
+    float es[3][3], dd[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < 3; ++a) {
+        es[i][a] = (float)e[0][i][a];
+        dd[i][a] = (float)Dm[i][a];
+      }
     // 6 edges + 4 spokes as combinations of the 3 base edges (v0 at 0):
     // positions 0, e1, e2, e3.  Length change via (lt^2 - ls^2)/(lt + ls).
     const float third = 1.0f / 3.0f;
@@ -200,45 +225,49 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
     def = (double)acc;
   }
 
-  // the two directions
+  // the two directions (unrolled so the vertex arrays stay in registers)
+#pragma unroll
   for (int d = 0; d < 2; ++d) {
     ItemRec& R = b.rec[2 * (size_t)tt + d];
     const double(*own)[3] = X[d];
     const double(*par)[3] = X[1 - d];
+    const double(*eo)[3] = e[d];
     const int* n = pr.n[d];
     const int* np = pr.n[1 - d];
     int flags = (vol6[d] > 0 && isfinite(vol6[d])) ? 1 : 0;
     R.prob = pi;
     R.tet = t;
     R.dir = d;
-    // map (FP64, oracle formula): G = [D1 D2 D3][r1;r2;r3]/det
-    double eo[3][3], D[3][3], r[3][3];
-    for (int i = 0; i < 3; ++i)
-      for (int a = 0; a < 3; ++a) {
-        eo[i][a] = e[d][i][a];
-        D[i][a] = dsub(e[1 - d][i][a], e[d][i][a]);
-      }
-    cross3d(eo[1], eo[2], r[0]);
-    cross3d(eo[2], eo[0], r[1]);
-    cross3d(eo[0], eo[1], r[2]);
-    double det = dot3d(eo[0], r[0]);
-    double inv = 1.0 / det;
-    double G64[3][3];
-    for (int c = 0; c < 3; ++c)
-      for (int j = 0; j < 3; ++j)
-        G64[c][j] = dmul(dadd(dmul(D[0][c], r[0][j]), dadd(dmul(D[1][c], r[1][j]), dmul(D[2][c], r[2][j]))), inv);
-    for (int c = 0; c < 3; ++c) {
-      for (int j = 0; j < 3; ++j) R.G64[c][j] = G64[c][j];
-      R.d0[c] = dsub(par[0][c], own[0][c]);
-    }
     for (int i = 0; i < 4; ++i)
-      for (int a = 0; a < 3; ++a) R.X[i][a] = own[i][a];
+      for (int a = 0; a < 3; ++a) {
+        R.X[i][a] = own[i][a];
+        R.XP[i][a] = par[i][a];
+      }
+    // map G = [D1 D2 D3][r1; r2; r3] / det for the FP32 path, with fused
+    // multiply-adds (within a few FP64 ulps of the exact-order map, which
+    // the decisions that need it rebuild from X and XP); det = 6V_own
+    const double sg = d == 0 ? 1.0 : -1.0;
+    double rr[3][3];
+    for (int j = 0; j < 3; ++j) rr[0][j] = r0[d][j];
+    rr[1][0] = fma(eo[2][1], eo[0][2], -eo[2][2] * eo[0][1]);
+    rr[1][1] = fma(eo[2][2], eo[0][0], -eo[2][0] * eo[0][2]);
+    rr[1][2] = fma(eo[2][0], eo[0][1], -eo[2][1] * eo[0][0]);
+    rr[2][0] = fma(eo[0][1], eo[1][2], -eo[0][2] * eo[1][1]);
+    rr[2][1] = fma(eo[0][2], eo[1][0], -eo[0][0] * eo[1][2]);
+    rr[2][2] = fma(eo[0][0], eo[1][1], -eo[0][1] * eo[1][0]);
+    const double inv = sg / vol6[d];
+    double Gd[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < 3; ++j) {
+        Gd[c][j] = fma(Dm[0][c], rr[0][j], fma(Dm[1][c], rr[1][j], Dm[2][c] * rr[2][j])) * inv;
+        R.Gd[c][j] = Gd[c][j];
+      }
     // linear-elastic energy from the source->target map (direction 0)
-    if (d == 0 && pr.model == 1 && det != 0.0 && isfinite(det)) {
+    if (d == 0 && pr.model == 1 && vol6[0] != 0.0 && isfinite(vol6[0])) {
       float H[3][3];
       for (int c = 0; c < 3; ++c)
         for (int j = 0; j < 3; ++j) {
-          float g = (float)G64[c][j] * pr.sp[1][c] / pr.sp[0][j];
+          float g = (float)Gd[c][j] * pr.sp[1][c] / pr.sp[0][j];
           if (c == j) g += pr.sp[1][c] / pr.sp[0][c] - 1.0f;
           H[c][j] = g;
         }
@@ -259,27 +288,33 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
       }
       continue;
     }
-    // bbox and origins
-    double lo[3], hi[3], plo[3];
+    // bbox and origins in FP32: rounding is monotone, so ceil/floor of the
+    // rounded extremes give a superset of the voxels the tet can hold
+    float lo[3], hi[3], plo[3], phi[3];
+    bool pfin = true;
     for (int a = 0; a < 3; ++a) {
-      lo[a] = hi[a] = own[0][a];
-      plo[a] = par[0][a];
+      lo[a] = hi[a] = (float)own[0][a];
+      plo[a] = phi[a] = (float)par[0][a];
+      pfin = pfin && isfinite(plo[a]);
       for (int i = 1; i < 4; ++i) {
-        lo[a] = fmin(lo[a], own[i][a]);
-        hi[a] = fmax(hi[a], own[i][a]);
-        plo[a] = fmin(plo[a], par[i][a]);
+        const float v = (float)own[i][a], w = (float)par[i][a];
+        lo[a] = fminf(lo[a], v);
+        hi[a] = fmaxf(hi[a], v);
+        plo[a] = fminf(plo[a], w);
+        phi[a] = fmaxf(phi[a], w);
+        pfin = pfin && isfinite(w);
       }
     }
     int O[3], Op[3];
     int L = 1;
     for (int a = 0; a < 3; ++a) {
-      double cl = ceil(lo[a]), fh = floor(hi[a]);
-      int b0 = cl < 0 ? 0 : (int)fmin(cl, (double)n[a]);
-      int b1 = fh > n[a] - 1 ? n[a] - 1 : (int)fmax(fh, -1.0);
+      float cl = ceilf(lo[a]), fh = floorf(hi[a]);
+      int b0 = cl < 0.f ? 0 : (int)fminf(cl, (float)n[a]);
+      int b1 = fh > (float)(n[a] - 1) ? n[a] - 1 : (int)fmaxf(fh, -1.0f);
       R.b0[a] = b0;
       R.b1[a] = b1;
-      O[a] = (int)fmax(fmin(floor(lo[a]), (double)n[a]), -2.0);
-      Op[a] = (int)fmax(fmin(floor(plo[a]), (double)np[a]), -2.0);
+      O[a] = (int)fmaxf(fminf(floorf(lo[a]), (float)n[a]), -2.0f);
+      Op[a] = (int)fmaxf(fminf(floorf(plo[a]), (float)np[a]), -2.0f);
       R.O[a] = O[a];
       R.Op[a] = Op[a];
       L = max(L, b1 - O[a] + 1);
@@ -287,69 +322,86 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
     R.b0[3] = R.b1[3] = R.O[3] = R.Op[3] = 0;
     if (R.b0[0] > R.b1[0] || R.b0[1] > R.b1[1] || R.b0[2] > R.b1[2]) flags = 0;
     R.flags = flags;
+    // own vertices relative to O: FP64 difference rounded once to FP32
+    float vr[4][3];
+    float V = 0.f;
     for (int i = 0; i < 4; ++i) {
-      for (int a = 0; a < 3; ++a) R.vr[i][a] = (float)dsub(own[i][a], (double)O[a]);
+      for (int a = 0; a < 3; ++a) {
+        vr[i][a] = (float)dsub(own[i][a], (double)O[a]);
+        R.vr[i][a] = vr[i][a];
+        V = fmaxf(V, fabsf(vr[i][a]));
+      }
       R.vr[i][3] = 0.f;
     }
-    // faces: inward normal in FP32, offset, certified margin
-    uint32_t fp = pr.fperm[t];
+    // faces: FP64 normals from the six edge vectors (fused cross products,
+    // within 2^-51 U W of the oracle's), rounded once to FP32; offset B from
+    // the FP32 relative vertex.  h(q) = A.q + B at a voxel q = p - O of the
+    // box (0 <= q < L) differs from the FP64 predicate by at most
+    //   eps (an (L + V) + 4 an V + 3 (an L + |B|)) + 1.5e-14 (U W + an)(L + V)
+    // (normal rounding over |q - a| <= L + V; vertex rounding and the FP32
+    // dot for B; the FP32 evaluation; the FP64 predicate's own rounding),
+    // eps = 2^-24 taken as 2^-22.
+    const double E6[6][3] = {{eo[0][0], eo[0][1], eo[0][2]},
+                             {eo[1][0], eo[1][1], eo[1][2]},
+                             {eo[2][0], eo[2][1], eo[2][2]},
+                             {dsub(own[2][0], own[1][0]), dsub(own[2][1], own[1][1]), dsub(own[2][2], own[1][2])},
+                             {dsub(own[3][0], own[1][0]), dsub(own[3][1], own[1][1]), dsub(own[3][2], own[1][2])},
+                             {dsub(own[3][0], own[2][0]), dsub(own[3][1], own[2][1]), dsub(own[3][2], own[2][2])}};
+    const uint32_t fp = pr.fperm[t];
+    const float Lf = (float)L;
+    const float e22 = 1.0f / 4194304.0f;
     for (int f = 0; f < 4; ++f) {
-      int ia = face_local(fp, f, 0), ib = face_local(fp, f, 1), ic = face_local(fp, f, 2);
-      int s = face_sign(fp, f);
-      double u[3], w[3], nn[3], ar[3];
+      const int ia = face_local(fp, f, 0), ib = face_local(fp, f, 1), ic = face_local(fp, f, 2);
+      const double s = (double)face_sign(fp, f);
+      double u[3], w[3];
       for (int a = 0; a < 3; ++a) {
-        u[a] = dsub(own[ib][a], own[ia][a]);
-        w[a] = dsub(own[ic][a], own[ia][a]);
-        ar[a] = dsub(own[ia][a], (double)O[a]);
+        u[a] = edge6(E6, ia, ib, a);
+        w[a] = edge6(E6, ia, ic, a);
       }
-      cross3d(u, w, nn);
-      double bp = -(double)s * dot3d(nn, ar);
-      float Ax = (float)(s * nn[0]), Ay = (float)(s * nn[1]), Az = (float)(s * nn[2]);
-      float Bp = (float)bp;
-      float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
-      float uw = fabs3max((float)u[0], (float)u[1], (float)u[2]) * fabs3max((float)w[0], (float)w[1], (float)w[2]);
-      float Lf = (float)(L + 1);
-      float mu = 1.0f / 524288.0f * (an * Lf + fabsf(Bp)) + 1.5e-14f * (uw + an) * Lf + 1e-30f;
+      const float Ax = (float)(s * fma(u[1], w[2], -u[2] * w[1]));
+      const float Ay = (float)(s * fma(u[2], w[0], -u[0] * w[2]));
+      const float Az = (float)(s * fma(u[0], w[1], -u[1] * w[0]));
+      float va[3];
+      for (int a = 0; a < 3; ++a) va[a] = pick4(vr, ia, a);
+      const float Bp = -fmaf(Ax, va[0], fmaf(Ay, va[1], Az * va[2]));
+      const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
+      const float UW = fabs3max((float)u[0], (float)u[1], (float)u[2]) * fabs3max((float)w[0], (float)w[1], (float)w[2]);
+      const float mu = e22 * (an * (4.0f * Lf + 5.0f * V) + 3.0f * fabsf(Bp)) +
+                       1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
       R.fa[f][0] = Ax;
       R.fa[f][1] = Ay;
       R.fa[f][2] = Az;
       R.fa[f][3] = Bp;
       R.fm[f][0] = mu;
       R.fm[f][1] = 1.0f / Ax;
-      R.fm[f][2] = 0.f;
-      R.fm[f][3] = 0.f;
+      R.fm[f][2] = e22 * 4.0f * an + 1.5e-14f * (UW + an);
+      // bound on |A.x - s n_x| beyond FP32 rounding: the fused and the
+      // oracle-order FP64 normals differ by a few 2^-53 U W
+      R.fm[f][3] = 3.0e-14f * UW + 1e-30f;
     }
     // FP32 map relative to the origins: p'_rel = vr + G vr + k
-    double kk[3];
-    double oo[3];
-    for (int a = 0; a < 3; ++a) oo[a] = dsub((double)O[a], own[0][a]);
     float gmax = 0.f, kmax = 0.f;
     for (int c = 0; c < 3; ++c) {
-      kk[c] = dadd(dadd((double)(O[c] - Op[c]), R.d0[c]),
-                   dadd(dmul(G64[c][0], oo[0]), dadd(dmul(G64[c][1], oo[1]), dmul(G64[c][2], oo[2]))));
+      const double oo0 = dsub((double)O[0], own[0][0]), oo1 = dsub((double)O[1], own[0][1]),
+                   oo2 = dsub((double)O[2], own[0][2]);
+      const double d0 = dsub(par[0][c], own[0][c]);
+      const double kk = ((double)(O[c] - Op[c]) + d0) + fma(Gd[c][0], oo0, fma(Gd[c][1], oo1, Gd[c][2] * oo2));
       for (int j = 0; j < 3; ++j) {
-        R.G[c][j] = (float)G64[c][j];
+        R.G[c][j] = (float)Gd[c][j];
         gmax = fmaxf(gmax, fabsf(R.G[c][j]));
       }
-      R.G[c][3] = (float)kk[c];
+      R.G[c][3] = (float)kk;
       kmax = fmaxf(kmax, fabsf(R.G[c][3]));
     }
     float M = (float)L * (1.0f + 3.0f * gmax) + kmax + 2.0f;
     // bit1: the partner tet lies within [-0.75, n - 0.25] on every axis and
     // the FP32 map error bound is far below 0.25 voxel, so no mapped voxel
-    // coordinate of this tet can leave [-1, n]
+    // coordinate of this tet can leave [-1, n].  fminf/fmaxf skip NaN, so
+    // finiteness is checked explicitly: a NaN partner vertex or map entry
+    // takes the clamped path.
     {
-      // fmin/fmax/fmaxf skip NaN, so finiteness is checked explicitly: a NaN
-      // partner vertex or map entry must take the clamped path
-      bool in = M < 4096.0f;
-      for (int a = 0; a < 3; ++a) {
-        double phi = par[0][a];
-        for (int i = 0; i < 4; ++i) {
-          in = in && isfinite(par[i][a]);
-          phi = fmax(phi, par[i][a]);
-        }
-        in = in && plo[a] >= -0.75 && phi <= (double)np[a] - 0.25;
-      }
+      bool in = M < 4096.0f && pfin;
+      for (int a = 0; a < 3; ++a) in = in && plo[a] >= -0.75f && phi[a] <= (float)np[a] - 0.25f;
       for (int c = 0; c < 3; ++c)
         for (int j = 0; j < 4; ++j) in = in && isfinite(R.G[c][j]);
       if (in) R.flags |= 2;
@@ -395,7 +447,8 @@ __device__ __forceinline__ bool rec_inside(const ItemRec& r, uint32_t fp, const 
   for (int f = 0; f < 4; ++f) {
     float h = fmaf(r.fa[f][0], px, fmaf(r.fa[f][1], py, fmaf(r.fa[f][2], pz, r.fa[f][3])));
     float an = fabsf(r.fa[f][0]) + fabsf(r.fa[f][1]) + fabsf(r.fa[f][2]);
-    float mu = r.fm[f][0] + an * (pmag + fabsf(px) + fabsf(py) + fabsf(pz) + 1.0f) * (1.0f / 1048576.0f);
+    float qm = fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz)));
+    float mu = r.fm[f][0] + r.fm[f][2] * qm + an * (pmag + fabsf(px) + fabsf(py) + fabsf(pz) + 1.0f) * (1.0f / 1048576.0f);
     if (h < -mu) return false;
     if (!(h > mu)) unc |= 1u << f;
   }
@@ -426,8 +479,11 @@ __device__ __forceinline__ bool vol_positive(const ItemRec& r) {
 }
 
 __device__ double landmark_term(const ItemRec& r, const DevProblem& pr, const double p[3], const double q[3]) {
+  // mapped landmark (v + d0) + G (v - own_0) with the record's FP64 map
   double pm[3];
-  map_exact(r, p, pm);
+  for (int c = 0; c < 3; ++c)
+    pm[c] = (p[c] + (r.XP[0][c] - r.X[0][c])) +
+            fma(r.Gd[c][0], p[0] - r.X[0][0], fma(r.Gd[c][1], p[1] - r.X[0][1], r.Gd[c][2] * (p[2] - r.X[0][2])));
   int dp = 1 - r.dir;
   double s = 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -526,7 +582,25 @@ void launch_reduce_full(const DevProblem* probs, int c0, int nc, const Batch& b,
 
 // Partial evaluation: one warp per trial relocates the landmarks whose
 // current tet is touched (or that are unlocated) among the touched tets.
-__global__ void k_landmarks_partial(const DevProblem* probs, Batch b) {
+// The trial's sorted touched-tet list is staged in shared memory so the
+// membership searches do not chain global loads.
+constexpr int kLmWarps = 8;
+constexpr int kLmTl = 256;  // staged list length per warp; longer lists search global memory
+
+__device__ __forceinline__ bool sorted_has(const int* tl, int n, int v) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int x = tl[mid];
+    if (x == v) return true;
+    if (x < v) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(32 * kLmWarps) k_landmarks_partial(const DevProblem* probs, Batch b) {
+  __shared__ int s_tl[kLmWarps][kLmTl];
   int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (k >= b.n_trials) return;
@@ -535,6 +609,12 @@ __global__ void k_landmarks_partial(const DevProblem* probs, Batch b) {
   const int cand = b.tr_cand[k];
   const int first = b.tr_first[k], ntt = b.tr_ntt[k];
   const int* tl = b.tt_tet + first;
+  int* stl = s_tl[threadIdx.x >> 5];
+  const bool staged = ntt <= kLmTl;
+  if (staged)
+    for (int j = lane; j < ntt; j += 32) stl[j] = tl[j];
+  __syncwarp();
+  const int* sl = staged ? stl : tl;
   int naff = 0;
   double gd = 0.0;
   int ud = 0;
@@ -545,20 +625,7 @@ __global__ void k_landmarks_partial(const DevProblem* probs, Batch b) {
     if (e < 2 * ng) {
       int mesh = e / ng, i = e % ng;
       told = pr.c_loc[((size_t)cand * 2 + mesh) * ng + i];
-      if (told < 0) aff = true;
-      else {
-        int lo = 0, hi = ntt - 1;
-        while (lo <= hi) {
-          int mid = (lo + hi) >> 1;
-          int v = tl[mid];
-          if (v == told) {
-            aff = true;
-            break;
-          }
-          if (v < told) lo = mid + 1;
-          else hi = mid - 1;
-        }
-      }
+      aff = told < 0 || sorted_has(sl, ntt, told);
     }
     unsigned am = __ballot_sync(FULL_MASK, aff);
     while (am) {
@@ -579,7 +646,7 @@ __global__ void k_landmarks_partial(const DevProblem* probs, Batch b) {
         bool in = false;
         if (j < ntt) {
           const ItemRec& r = b.rec[2 * (size_t)(first + j) + mesh];
-          in = lm_test(r, pr.fperm[tl[j]], p, pmag);
+          in = lm_test(r, pr.fperm[sl[j]], p, pmag);
         }
         unsigned m = __ballot_sync(FULL_MASK, in);
         if (m) found = jb + __ffs(m) - 1;
@@ -593,7 +660,7 @@ __global__ void k_landmarks_partial(const DevProblem* probs, Batch b) {
         if (naff < b.aff_cap) {
           size_t o = (size_t)k * b.aff_cap + naff;
           b.aff_idx[o] = ee;
-          b.aff_loc[o] = found >= 0 ? tl[found] : -1;
+          b.aff_loc[o] = found >= 0 ? sl[found] : -1;
           b.aff_term[o] = term;
         }
         ++naff;
@@ -610,19 +677,27 @@ __global__ void k_landmarks_partial(const DevProblem* probs, Batch b) {
 void launch_landmarks_partial(const DevProblem* probs, const Batch& b, cudaStream_t st) {
   if (b.n_trials <= 0) return;
   long threads = 32L * b.n_trials;
-  k_landmarks_partial<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(probs, b);
+  k_landmarks_partial<<<(unsigned)((threads + 32 * kLmWarps - 1) / (32 * kLmWarps)), 32 * kLmWarps, 0, st>>>(probs, b);
 }
 
 // Partial evaluation: new = stored - sum old + sum new over touched tets.
+// One warp per trial: lanes take the touched tets, FP64 warp sums.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = dadd(v, __shfl_xor_sync(FULL_MASK, v, o));
+  return v;
+}
+
 __global__ void k_reduce_partial(const DevProblem* probs, Batch b, int has_landmarks) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
   if (k >= b.n_trials) return;
   const DevProblem& pr = probs[b.tr_prob ? b.tr_prob[k] : 0];
   const int cand = b.tr_cand[k];
   const int first = b.tr_first[k], ntt = b.tr_ntt[k];
   double old[3] = {0, 0, 0}, nw[3] = {0, 0, 0};
-  unsigned long long cov = 0;
-  for (int j = 0; j < ntt; ++j) {
+  unsigned cov = 0;
+  for (int j = lane; j < ntt; j += 32) {
     int tt = first + j;
     size_t ci = (size_t)cand * pr.ntet + b.tt_tet[tt];
     old[0] = dadd(old[0], dadd(pr.c_ssd[2 * ci], pr.c_ssd[2 * ci + 1]));
@@ -633,6 +708,12 @@ __global__ void k_reduce_partial(const DevProblem* probs, Batch b, int has_landm
     nw[2] = dadd(nw[2], (double)b.o_fold[tt]);
     cov += (unsigned)(b.o_cov[2 * (size_t)tt] + b.o_cov[2 * (size_t)tt + 1]);
   }
+  for (int q = 0; q < 3; ++q) {
+    old[q] = warp_sum_d(old[q]);
+    nw[q] = warp_sum_d(nw[q]);
+  }
+  cov = __reduce_add_sync(FULL_MASK, cov);
+  if (lane != 0) return;
   double* dl = b.tr_delta + 4 * (size_t)k;
   dl[0] = dsub(nw[0], old[0]);
   dl[1] = dsub(nw[1], old[1]);
@@ -646,12 +727,13 @@ __global__ void k_reduce_partial(const DevProblem* probs, Batch b, int has_landm
   ob[1] = dadd(s[1], dl[1]) / pr.def_norm;
   ob[2] = pr.ng > 0 ? dadd(s[2], gd) / pr.guid_norm : 0.0;
   ob[3] = dadd(s[3], dl[3]);
-  atomicAdd(pr.samples, cov);
+  atomicAdd(pr.samples, (unsigned long long)cov);
 }
 
 void launch_reduce_partial(const DevProblem* probs, const Batch& b, cudaStream_t st) {
   if (b.n_trials <= 0) return;
-  k_reduce_partial<<<(b.n_trials + 127) / 128, 128, 0, st>>>(probs, b, b.aff_n != nullptr);
+  long threads = 32L * b.n_trials;
+  k_reduce_partial<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(probs, b, b.aff_n != nullptr);
 }
 
 // Accept-if-improves (Sec. 2.2), constraint domination first.
@@ -678,7 +760,7 @@ void launch_accept(const DevProblem* probs, const Batch& b, uint8_t* accept, cud
 }
 
 // Commit: per touched tet (cache), per trial (coords, landmarks), per
-// candidate (ordered sum of accepted deltas).
+// candidate (sum of the accepted deltas).
 __global__ void k_commit_tt(const DevProblem* probs, Batch b, const uint8_t* accept) {
   int tt = blockIdx.x * blockDim.x + threadIdx.x;
   if (tt >= b.n_tt) return;
@@ -719,17 +801,31 @@ __global__ void k_commit_trial(const DevProblem* probs, Batch b, const uint8_t* 
   }
 }
 
+// One warp per candidate: the accepted trials' deltas (independent groups)
+// summed over the warp, then added to the stored sums.
 __global__ void k_commit_sums(const DevProblem* probs, Batch b, const uint8_t* accept, const int* cand_ptr,
                               const int* cand_trials, int n_list) {
-  int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  int ci = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
   if (ci >= n_list) return;
-  int k0 = cand_trials[cand_ptr[ci]];
+  const int j0 = cand_ptr[ci], j1 = cand_ptr[ci + 1];
+  if (j1 <= j0) return;
+  int k0 = cand_trials[j0];
   const DevProblem& pr = probs[b.tr_prob ? b.tr_prob[k0] : 0];
-  double* s = pr.sums + 4 * (size_t)b.tr_cand[k0];
-  for (int j = cand_ptr[ci]; j < cand_ptr[ci + 1]; ++j) {
-    int k = cand_trials[j];
-    if (!accept[k]) continue;
-    for (int q = 0; q < 4; ++q) s[q] = dadd(s[q], b.tr_delta[4 * (size_t)k + q]);
+  double tot[4] = {0, 0, 0, 0};
+  for (int jb = j0; jb < j1; jb += 32) {
+    int j = jb + lane;
+    double d[4] = {0, 0, 0, 0};
+    if (j < j1) {
+      int k = cand_trials[j];
+      if (accept[k])
+        for (int q = 0; q < 4; ++q) d[q] = b.tr_delta[4 * (size_t)k + q];
+    }
+    for (int q = 0; q < 4; ++q) tot[q] = dadd(tot[q], warp_sum_d(d[q]));
+  }
+  if (lane == 0) {
+    double* s = pr.sums + 4 * (size_t)b.tr_cand[k0];
+    for (int q = 0; q < 4; ++q) s[q] = dadd(s[q], tot[q]);
   }
 }
 
@@ -739,7 +835,7 @@ void launch_commit(const DevProblem* probs, const Batch& b, const uint8_t* accep
   if (b.n_trials <= 0) return;
   k_commit_tt<<<(b.n_tt + 255) / 256, 256, 0, st>>>(probs, b, accept);
   k_commit_trial<<<b.n_trials, 64, 0, st>>>(probs, b, accept, tr_group, g_ptr, g_pts);
-  k_commit_sums<<<(n_list + 127) / 128, 128, 0, st>>>(probs, b, accept, cand_ptr, cand_trials, n_list);
+  k_commit_sums<<<(unsigned)((32L * n_list + 255) / 256), 256, 0, st>>>(probs, b, accept, cand_ptr, cand_trials, n_list);
 }
 
 // Proposal for generation plans: trial coords = committed group coords + delta.
