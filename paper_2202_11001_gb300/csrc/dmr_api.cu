@@ -89,6 +89,7 @@ struct Scratch {
   int* cand_ptr = nullptr;
   int* cand_trials = nullptr;
   unsigned* work = nullptr;
+  int* slow = nullptr;
 
   void release() {
     dfree(rec); dfree(o_ssd); dfree(o_cov); dfree(o_def); dfree(o_fold);
@@ -96,6 +97,7 @@ struct Scratch {
     dfree(tr_cand); dfree(tr_first); dfree(tr_ntt); dfree(tr_group); dfree(tr_coords);
     dfree(aff_n); dfree(aff_idx); dfree(aff_loc); dfree(aff_term);
     dfree(tr_delta); dfree(tr_obj); dfree(accept); dfree(cand_ptr); dfree(cand_trials); dfree(work);
+    dfree(slow);
     cap_tt = cap_tr = 0;
   }
 
@@ -115,7 +117,7 @@ struct Scratch {
         (rc = dalloc(&aff_term, (size_t)nr * std::max(a, 1))) || (rc = dalloc(&tr_delta, (size_t)nr * 4)) ||
         (rc = dalloc(&tr_obj, (size_t)nr * 4)) || (rc = dalloc(&accept, (size_t)nr)) ||
         (rc = dalloc(&cand_ptr, (size_t)nr + 1)) || (rc = dalloc(&cand_trials, (size_t)nr)) ||
-        (rc = dalloc(&work, 1))) {
+        (rc = dalloc(&work, 4)) || (rc = dalloc(&slow, 2 * (size_t)nt))) {
       release();
       return rc;
     }
@@ -132,6 +134,9 @@ struct Scratch {
 struct dmr_problem {
   int dev = 0;
   cudaStream_t st = nullptr;
+  // side stream for landmark relocation beside the raster kernels (lazy)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int n_sm = 1;
   int P = 0, ntet = 0, m[3] = {0, 0, 0};
   int n[2][3];
@@ -150,6 +155,7 @@ struct dmr_problem {
   void* plain[2] = {nullptr, nullptr};
   void* cells[2] = {nullptr, nullptr};
   uint8_t* cflag[2] = {nullptr, nullptr};
+  unsigned long long* cmask[2] = {nullptr, nullptr};
   int4* d_tet = nullptr;
   uint32_t* d_fperm = nullptr;
   uint8_t* d_fix = nullptr;
@@ -288,6 +294,7 @@ void release_problem(dmr_problem* p) {
     dfree(p->plain[k]);
     dfree(p->cells[k]);
     dfree(p->cflag[k]);
+    dfree(p->cmask[k]);
   }
   dfree(p->d_tet); dfree(p->d_fperm); dfree(p->d_fix); dfree(p->d_restvol); dfree(p->d_guide);
   dfree(p->d_coords); dfree(p->d_ssd); dfree(p->d_cov); dfree(p->d_def); dfree(p->d_fold);
@@ -384,6 +391,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
     if ((rc = dalloc((char**)&p->plain[k], nv * dtype_size(p->storage)))) goto fail_;
     if ((rc = dalloc((char**)&p->cells[k], nc * 8 * dtype_size(p->storage)))) goto fail_;
     if ((rc = dalloc(&p->cflag[k], nc))) goto fail_;
+    if ((rc = dalloc(&p->cmask[k], nc))) goto fail_;
     void* src = (void*)d->img[k];
     void* tmp = nullptr;
     if (!is_device_ptr(src)) {
@@ -392,7 +400,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       src = tmp;
     }
     launch_convert_image(src, d->img_dtype, p->plain[k], p->storage, nv, p->st);
-    launch_build_cells(p->plain[k], p->storage, p->n[k], p->cells[k], p->cflag[k], p->st);
+    launch_build_cells(p->plain[k], p->storage, p->n[k], p->cells[k], p->cflag[k], p->cmask[k], p->st);
     if (tmp) {
       cudaStreamSynchronize(p->st);
       cudaFree(tmp);
@@ -461,6 +469,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       h.plain[k] = p->plain[k];
       h.cells[k] = p->cells[k];
       h.cflag[k] = p->cflag[k];
+      h.cmask[k] = p->cmask[k];
       for (int a = 0; a < 3; ++a) {
         h.n[k][a] = p->n[k][a];
         h.spd[k][a] = p->sp[k][a];
@@ -512,6 +521,12 @@ fail_:
 int dmr_problem_destroy(dmr_problem* p) {
   if (!p) return DMR_OK;
   cudaStreamSynchronize(p->st);
+  if (p->st2) {
+    cudaStreamSynchronize(p->st2);
+    cudaStreamDestroy(p->st2);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   release_problem(p);
   delete p;
   return DMR_OK;
@@ -684,6 +699,7 @@ Batch make_batch(dmr_problem* p, Scratch& s, int n_tt, int n_tr) {
   b.o_def = s.o_def;
   b.o_fold = s.o_fold;
   b.work = s.work;
+  b.slow = s.slow;
   b.aff_cap = s.aff_cap;
   b.aff_n = p->ng > 0 ? s.aff_n : nullptr;
   b.aff_idx = s.aff_idx;
@@ -820,8 +836,20 @@ int dmr_eval_partial(dmr_problem* p, int n_trials, const int* group_ids, const i
                      st));
   Batch b = make_batch(p, p->sc, (int)tot, n_trials);
   launch_setup(p->d_prob, b, st);
-  launch_raster(p->d_prob, b, p->storage, p->warps, p->vpw, p->n_sm, st);
-  if (p->ng > 0) launch_landmarks_partial(p->d_prob, b, st);
+  if (p->ng > 0 && !p->st2) {
+    CU(cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  }
+  // landmark relocation needs only the set-up records: it runs on a side
+  // stream beside the raster kernels that complete deferred work
+  launch_raster(p->d_prob, b, p->storage, p->warps, p->vpw, p->n_sm, st, p->ng > 0 ? p->st2 : nullptr,
+                p->ev_fork);
+  if (p->ng > 0) {
+    launch_landmarks_partial(p->d_prob, b, p->st2);
+    CU(cudaEventRecord(p->ev_join, p->st2));
+    CU(cudaStreamWaitEvent(st, p->ev_join, 0));
+  }
   launch_reduce_partial(p->d_prob, b, st);
   CU(cudaGetLastError());
   bool host_dst;
@@ -1009,7 +1037,7 @@ int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, flo
     for (int j = 0; j < 3; ++j) {
       float tot = 0.f;
       for (int rep = 0; rep < 4; ++rep) {
-        cudaMemsetAsync(b.work, 0, sizeof(unsigned), st);
+        cudaMemsetAsync(b.work, 0, 3 * sizeof(unsigned), st);
         cudaEventRecord(e0, st);
         launch_raster(p->d_prob, b, p->storage, W[i], V[j], p->n_sm, st);
         cudaEventRecord(e1, st);
@@ -1154,6 +1182,20 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
     dmr_plan_destroy(pl);
     return fail(DMR_ECUDA, "stream create failed");
   }
+  // side branch of the graph: landmark relocation needs only the set-up
+  // records, so it runs beside the raster kernels
+  cudaStream_t cs2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  if (cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (cs2) cudaStreamDestroy(cs2);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    cudaStreamDestroy(cs);
+    dmr_plan_destroy(pl);
+    return fail(DMR_ECUDA, "stream create failed");
+  }
   for (dmr_problem* p : probs) cudaStreamSynchronize(p->st);
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   int launches = 0;
@@ -1174,11 +1216,15 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
     cudaEventRecordWithFlags(pl->ev[3 * w], cs, cudaEventRecordExternal);
     launch_setup(d_probs, b, cs);
     cudaEventRecordWithFlags(pl->ev[3 * w + 1], cs, cudaEventRecordExternal);
-    launch_raster(d_probs, b, p0->storage, p0->warps, p0->vpw, p0->n_sm, cs);
+    launch_raster(d_probs, b, p0->storage, p0->warps, p0->vpw, p0->n_sm, cs, any_ng ? cs2 : nullptr,
+                  any_ng ? ev_fork : nullptr);
     cudaEventRecordWithFlags(pl->ev[3 * w + 2], cs, cudaEventRecordExternal);
-    launches += 3;
+    launches += 2 + kRasterLaunches;
     if (any_ng) {
-      launch_landmarks_partial(d_probs, b, cs);
+      // the fork is recorded inside launch_raster after the fast kernel
+      launch_landmarks_partial(d_probs, b, cs2);
+      cudaEventRecord(ev_join, cs2);
+      cudaStreamWaitEvent(cs, ev_join, 0);
       ++launches;
     }
     launch_reduce_partial(d_probs, b, cs);
@@ -1191,6 +1237,9 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
   cudaStreamDestroy(cs);
+  cudaStreamDestroy(cs2);
+  cudaEventDestroy(ev_fork);
+  cudaEventDestroy(ev_join);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
     dmr_plan_destroy(pl);

@@ -158,17 +158,30 @@ static __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
+// Shared-memory load of 4 floats that the compiler may not hoist or merge:
+// the record stays in shared memory instead of occupying registers across
+// the row and voxel loops.
+static __device__ __forceinline__ float4 lds4(const float* p) {
+  float4 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+
 // y-range of slice z (relative to O) through the tet: min/max over edges
 // crossing the plane; a superset (slack) of the rows holding inside voxels.
 static __device__ __forceinline__ void slice_yrange(const ItemRec& r, float zr, float& ylo, float& yhi) {
   ylo = 3.0e38f;
   yhi = -3.0e38f;
+  float4 v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = lds4(&r.vr[i][0]);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = i + 1; j < 4; ++j) {
-      float zi = r.vr[i][2], zj = r.vr[j][2];
-      float yi = r.vr[i][1], yj = r.vr[j][1];
+      float zi = v[i].z, zj = v[j].z;
+      float yi = v[i].y, yj = v[j].y;
       if ((zi - zr) * (zj - zr) <= 0.f) {
         float y;
         if (zj != zi) {
@@ -243,52 +256,64 @@ static __device__ __noinline__ void span_careful(const ItemRec& r, uint32_t fp, 
 // it: all voxels of [lo, hi] certainly inside every face, and the voxel just
 // outside each end certainly outside its binding face (h is monotone in x,
 // so that settles the whole row).  Otherwise the careful path decides.
+template <bool FAST>
 static __device__ __forceinline__ void row_span(const ItemRec& r, uint32_t fp, int xl, int xh, int yi, int zi,
-                                                int& lo, int& hi) {
+                                                int& lo, int& hi, bool& careful) {
   const float yr = (float)yi, zr = (float)zi;
   lo = xl;
   hi = xh;
-  int fl = -1, fh = -1;
   bool ok = true;
-  float c[4];
+  // binding faces of the two ends: (A.x, h at x = 0, margin)
+  float Al = 0.f, cl = 0.f, ml = 0.f, Ah = 0.f, ch = 0.f, mh = 0.f;
+  bool hasl = false, hash = false;
+  float Av[4], cv[4], mv[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    const float Ax = r.fa[f][0];
-    c[f] = fmaf(r.fa[f][1], yr, fmaf(r.fa[f][2], zr, r.fa[f][3]));
-    const float mu = r.fm[f][0];
-    if (Ax == 0.f) {
-      if (c[f] < -mu) {
+    const float4 A = lds4(&r.fa[f][0]);
+    const float4 M = lds4(&r.fm[f][0]);
+    Av[f] = A.x;
+    cv[f] = fmaf(A.y, yr, fmaf(A.z, zr, A.w));
+    mv[f] = M.x;
+    if (A.x == 0.f) {
+      if (cv[f] < -M.x) {
         hi = xl - 1;
-        fh = -2;
-      } else if (!(c[f] > mu)) {
+        hash = false;
+      } else if (!(cv[f] > M.x)) {
         ok = false;
       }
       continue;
     }
-    float th = fminf(fmaxf(-c[f] * r.fm[f][1], (float)(xl - 1)), (float)(xh + 1));
+    float th = fminf(fmaxf(-cv[f] * M.y, (float)(xl - 1)), (float)(xh + 1));
     int kb;
     (void)ffloor_magic(th, kb);
     const int k = kb - MAGIC_BITS;
-    if (Ax > 0.f) {
+    if (A.x > 0.f) {
       if (k + 1 > lo) {
         lo = k + 1;
-        fl = f;
+        Al = A.x;
+        cl = cv[f];
+        ml = M.x;
+        hasl = true;
       }
     } else if (k < hi) {
       hi = k;
-      fh = f;
+      Ah = A.x;
+      ch = cv[f];
+      mh = M.x;
+      hash = true;
     }
   }
   if (lo <= hi) {
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const float Ax = r.fa[f][0];
-      if (Ax != 0.f) ok = ok && fmaf(Ax, (float)(Ax > 0.f ? lo : hi), c[f]) > r.fm[f][0];
-    }
+    for (int f = 0; f < 4; ++f)
+      if (Av[f] != 0.f) ok = ok && fmaf(Av[f], (float)(Av[f] > 0.f ? lo : hi), cv[f]) > mv[f];
   }
-  if (fl >= 0 && lo - 1 >= xl) ok = ok && fmaf(r.fa[fl][0], (float)(lo - 1), c[fl]) < -r.fm[fl][0];
-  if (fh >= 0 && hi + 1 <= xh) ok = ok && fmaf(r.fa[fh][0], (float)(hi + 1), c[fh]) < -r.fm[fh][0];
-  if (!ok) span_careful(r, fp, xl, xh, yi, zi, lo, hi);
+  if (hasl && lo - 1 >= xl) ok = ok && fmaf(Al, (float)(lo - 1), cl) < -ml;
+  if (hash && hi + 1 <= xh) ok = ok && fmaf(Ah, (float)(hi + 1), ch) < -mh;
+  careful = !ok;
+  if constexpr (!FAST) {
+    if (!ok) span_careful(r, fp, xl, xh, yi, zi, lo, hi);
+  }
 }
 
 // Black decision of one sample where the FP32 cell cannot decide it: FP64
@@ -371,6 +396,46 @@ static __device__ __forceinline__ float cell_interp(const Cell<ST>& c, float fx,
   return fmaf(fz, b1 - b0, b0);
 }
 
+// Black decision of a sample whose FP32 fraction is within delta of 0 or 1
+// on some axis, from the zero mask of the 4x4x4 block around its cell.  Per
+// axis the true support is {i, i+1} unless the fraction is near 0 (then
+// {i-1, i}, {i} or {i, i+1}) or near 1 ({i, i+1}, {i+1} or {i+1, i+2}).
+// Black for certain if the union of the possible supports is all 0; not
+// black for certain if their intersection holds a nonzero voxel.  Returns
+// 1 / 0, or -1 when the FP64 definition must decide.
+static __device__ __forceinline__ int black_near(unsigned long long zm, float fx, float fy, float fz, float delta) {
+  // 4-bit sets over the offsets -1..2 (bit 0 = offset -1)
+  auto axis = [&](float f, unsigned& un, unsigned& in) {
+    if (f <= delta) {
+      un = 0x7u;
+      in = 0x2u;
+    } else if (f >= 1.0f - delta) {
+      un = 0xEu;
+      in = 0x4u;
+    } else {
+      un = in = 0x6u;
+    }
+  };
+  unsigned ux, ix, uy, iy, uz, iz;
+  axis(fx, ux, ix);
+  axis(fy, uy, iy);
+  axis(fz, uz, iz);
+  auto box = [](unsigned mx, unsigned my, unsigned mz) {
+    // rows of 4 bits: (y, z) -> bits 4 y + 16 z
+    unsigned long long row = 0ull;
+    for (int y = 0; y < 4; ++y)
+      if ((my >> y) & 1u) row |= (unsigned long long)mx << (4 * y);
+    unsigned long long m = 0ull;
+    for (int z = 0; z < 4; ++z)
+      if ((mz >> z) & 1u) m |= row << (16 * z);
+    return m;
+  };
+  const unsigned long long U = box(ux, uy, uz), I = box(ix, iy, iz);
+  if ((zm & U) == U) return 1;
+  if ((zm & I) != I) return 0;
+  return -1;
+}
+
 // Cell flags (built with the corner cells): bit0 some corner is 0, bit1 all
 // corners are 0, bit2 every voxel of the 4x4x4 block around the cell is 0,
 // bit3 no voxel of that block is 0.  The exact support of a sample always
@@ -382,8 +447,16 @@ enum { CF_ANY0 = 1, CF_ALL0 = 2, CF_NB_ALL0 = 4, CF_NB_NONE0 = 8 };
 #define DMR_RASTER_THREADS_PER_SM 768
 #endif
 
-template <int ST, int WARPS, int VPL>
-__global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARPS * 32) > 0
+// Two kernels share this body.  FAST = true: no function calls in the row
+// and voxel loops (a call there costs ~60 registers per thread, a third of
+// the SM's resident warps); an item with a row whose span the margins cannot
+// certify, or a sample whose black decision needs the FP64 definition, is
+// abandoned and appended to b.slow.  FAST = false: the same item logic with
+// the careful span and the exact black decision inline, over the items of
+// b.slow.  Which items are handed over depends only on the data, so results
+// do not depend on the tile shape.
+template <int ST, int WARPS, int VPL, bool FAST>
+__global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM / (WARPS * 32) > 0
                                                     ? DMR_RASTER_THREADS_PER_SM / (WARPS * 32)
                                                     : 1))
     k_raster(const DevProblem* __restrict__ probs, Batch b) {
@@ -394,7 +467,14 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
   const int n_items = 2 * b.n_tt;
   for (;;) {
     int item = 0;
-    if (lane == 0) item = (int)atomicAdd(b.work, 1u);
+    if (lane == 0) {
+      if constexpr (FAST) {
+        item = (int)atomicAdd(b.work, 1u);
+      } else {
+        const unsigned w = atomicAdd(b.work + 2, 1u);
+        item = w < *(volatile unsigned*)(b.work + 1) ? b.slow[w] : n_items;
+      }
+    }
     item = __shfl_sync(FULL_MASK, item, 0);
     if (item >= n_items) break;
     {
@@ -407,6 +487,7 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
     const ItemRec& r = ws->rec;
     float sum = 0.f, comp = 0.f;
     int cov = 0;
+    bool need_exact = false;  // FAST: some sample needs the FP64 black decision
     if (r.flags & 1) {
       const DevProblem& pr = probs[r.prob];
       const int d = r.dir;
@@ -414,6 +495,7 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
       const void* own_img = pr.plain[d];
       const void* cells = pr.cells[1 - d];
       const uint8_t* cflag = pr.cflag[1 - d];
+      const unsigned long long* cmask = pr.cmask[1 - d];
       const int nxo = pr.n[d][0], nyo = pr.n[d][1];
       const unsigned Sy = (unsigned)(pr.n[1 - d][0] + 2), Sz = (unsigned)(pr.n[1 - d][1] + 2) * Sy;
       const bool black = pr.black_rule != 0;
@@ -453,13 +535,17 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
           const int zrow = zb + s;
           const int yrow = yl_s + (rq - e_s);
           int xcnt = 0, x0 = 0;
+          bool careful = false;
           if (has_row) {
             int lo, hi;
-            row_span(r, fp, xl, xh, yrow - Oy, zrow - Oz, lo, hi);
+            row_span<FAST>(r, fp, xl, xh, yrow - Oy, zrow - Oz, lo, hi, careful);
             if (hi >= lo) {
               xcnt = hi - lo + 1;
               x0 = lo + Ox;
             }
+          }
+          if constexpr (FAST) {
+            if (__any_sync(FULL_MASK, careful)) goto handover;
           }
           const unsigned nzm = __ballot_sync(FULL_MASK, xcnt > 0);
           const int cidx = __popc(nzm & (lemask >> 1));
@@ -468,9 +554,10 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
           const int T = __shfl_sync(FULL_MASK, xincl, 31);
           if (xcnt > 0) {
             const float vx = (float)(x0 - Ox), vy = (float)(yrow - Oy), vz = (float)(zrow - Oz);
-            const float px = vx + fmaf(r.G[0][0], vx, fmaf(r.G[0][1], vy, fmaf(r.G[0][2], vz, r.G[0][3])));
-            const float py = vy + fmaf(r.G[1][0], vx, fmaf(r.G[1][1], vy, fmaf(r.G[1][2], vz, r.G[1][3])));
-            const float pz = vz + fmaf(r.G[2][0], vx, fmaf(r.G[2][1], vy, fmaf(r.G[2][2], vz, r.G[2][3])));
+            const float4 g0 = lds4(&r.G[0][0]), g1 = lds4(&r.G[1][0]), g2 = lds4(&r.G[2][0]);
+            const float px = vx + fmaf(g0.x, vx, fmaf(g0.y, vy, fmaf(g0.z, vz, g0.w)));
+            const float py = vy + fmaf(g1.x, vx, fmaf(g1.y, vy, fmaf(g1.z, vz, g1.w)));
+            const float pz = vz + fmaf(g2.x, vx, fmaf(g2.y, vy, fmaf(g2.z, vz, g2.w)));
             ws->meta[cidx] = make_int2(xexcl, (zrow * nyo + yrow) * nxo + x0);
             ws->pr0[cidx] = make_float4(px, py, pz, 0.f);
           }
@@ -510,6 +597,7 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
             float own[VPL], fx[VPL], fy[VPL], fz[VPL];
             uint8_t cf[VPL];
             int oi[VPL];
+            unsigned cix[VPL];
 #pragma unroll
             for (int u = 0; u < VPL; ++u) {
               if (vv[u] < T) {
@@ -529,6 +617,7 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
                 fy[u] = py - fly;
                 fz[u] = pz - flz;
                 const unsigned ci = cbase + (unsigned)iz * Sz + (unsigned)iy * Sy + (unsigned)ix;
+                cix[u] = ci;
                 oi[u] = mt.y + dx;
                 cell_load<ST>(cells, ci, cell[u]);
                 own[u] = load_plain<ST>(own_img, oi[u]);
@@ -551,14 +640,22 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
                   } else if (!(f & CF_ANY0)) {
                     blk = false;
                   } else {
-                    const bool nearp = fminf(fminf(fx[u], fy[u]), fz[u]) < delta ||
-                                       fmaxf(fmaxf(fx[u], fy[u]), fz[u]) > 1.0f - delta;
+                    const bool nearp = fminf(fminf(fx[u], fy[u]), fz[u]) <= delta ||
+                                       fmaxf(fmaxf(fx[u], fy[u]), fz[u]) >= 1.0f - delta;
                     if (!nearp) {
                       blk = (f & CF_ALL0) != 0;
                     } else {
-                      const int xa = oi[u] % nxo;
-                      const int rem = oi[u] / nxo;
-                      blk = black_exact(r, pr, xa, rem % nyo, rem / nyo);
+                      const int dec = black_near(__ldg(cmask + cix[u]), fx[u], fy[u], fz[u], delta);
+                      if (dec >= 0) {
+                        blk = dec != 0;
+                      } else if constexpr (FAST) {
+                        need_exact = true;
+                        blk = false;
+                      } else {
+                        const int xa = oi[u] % nxo;
+                        const int rem = oi[u] / nxo;
+                        blk = black_exact(r, pr, xa, rem % nyo, rem / nyo);
+                      }
                     }
                   }
                   if ((o == 0.0f) != blk) d2 = 1.0f;
@@ -566,6 +663,9 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
                 bsum += d2;
                 ++cov;
               }
+            }
+            if constexpr (FAST) {
+              if (__any_sync(FULL_MASK, need_exact)) goto handover;
             }
           }
           {
@@ -578,55 +678,73 @@ __global__ void __launch_bounds__(WARPS * 32, (DMR_RASTER_THREADS_PER_SM / (WARP
         }
       }
     }
-    // error-free warp reduction of (sum, -comp)
-    float hi = sum, lo = -comp;
+    {
+      // error-free warp reduction of (sum, -comp)
+      float hi = sum, lo = -comp;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oh = __shfl_xor_sync(FULL_MASK, hi, o);
-      const float ol = __shfl_xor_sync(FULL_MASK, lo, o);
-      const float sh = hi + oh;
-      const float bb = sh - hi;
-      const float err = (hi - (sh - bb)) + (oh - bb);
-      hi = sh;
-      lo = lo + ol + err;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(FULL_MASK, hi, o);
+        const float ol = __shfl_xor_sync(FULL_MASK, lo, o);
+        const float sh = hi + oh;
+        const float bb = sh - hi;
+        const float err = (hi - (sh - bb)) + (oh - bb);
+        hi = sh;
+        lo = lo + ol + err;
+      }
+      const int covt = __reduce_add_sync(FULL_MASK, cov);
+      __syncwarp();
+      if (lane == 0) {
+        b.o_ssd[item] = (double)hi + (double)lo;
+        b.o_cov[item] = covt;
+      }
+      __syncwarp();
     }
-    const int covt = __reduce_add_sync(FULL_MASK, cov);
-    if (lane == 0) {
-      b.o_ssd[item] = (double)hi + (double)lo;
-      b.o_cov[item] = covt;
-    }
+    continue;
+  handover:
+    // FAST only: the item goes to the full-logic kernel, which writes its outputs
+    if (lane == 0) b.slow[atomicAdd(b.work + 1, 1u)] = item;
     __syncwarp();
   }
 }
 
-template <int ST, int WARPS, int VPL>
+template <int ST, int WARPS, int VPL, bool FAST>
 static void raster_launch_one(const DevProblem* probs, const Batch& b, int n_sm, cudaStream_t st) {
   const int threads = 32 * WARPS;
   const size_t smem = sizeof(WarpSmem) * WARPS;
   const long items = 2L * b.n_tt;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster<ST, WARPS, VPL>, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster<ST, WARPS, VPL, FAST>, threads, smem);
   if (per_sm < 1) per_sm = 1;
   long blocks = (long)n_sm * per_sm;
   const long need = (items + WARPS - 1) / WARPS;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  k_raster<ST, WARPS, VPL><<<(unsigned)blocks, threads, smem, st>>>(probs, b);
+  k_raster<ST, WARPS, VPL, FAST><<<(unsigned)blocks, threads, smem, st>>>(probs, b);
 }
 
+// The fast kernel with the requested tile shape, then the full-logic kernel
+// over the items it handed over (a persistent grid that exits at once when
+// there are none).
 template <int ST>
-static void raster_launch(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st) {
+static void raster_launch(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st,
+                          cudaStream_t side, cudaEvent_t fork) {
   const int vpl = vpw >= 128 ? 4 : (vpw >= 64 ? 2 : 1);
+  bool done = false;
 #define DMR_RL(W, V)                                          \
-  if (warps == W && vpl == V) {                               \
-    raster_launch_one<ST, W, V>(probs, b, n_sm, st);          \
-    return;                                                   \
+  if (!done && warps == W && vpl == V) {                      \
+    raster_launch_one<ST, W, V, true>(probs, b, n_sm, st);    \
+    done = true;                                              \
   }
   DMR_RL(4, 1) DMR_RL(4, 2) DMR_RL(4, 4)
   DMR_RL(8, 1) DMR_RL(8, 2) DMR_RL(8, 4)
   DMR_RL(16, 1) DMR_RL(16, 2) DMR_RL(16, 4)
 #undef DMR_RL
-  raster_launch_one<ST, 8, 2>(probs, b, n_sm, st);
+  if (!done) raster_launch_one<ST, 4, 1, true>(probs, b, n_sm, st);
+  if (side && fork) {
+    cudaEventRecord(fork, st);
+    cudaStreamWaitEvent(side, fork, 0);
+  }
+  raster_launch_one<ST, 4, 1, false>(probs, b, n_sm, st);
 }
 
 }  // namespace dmr

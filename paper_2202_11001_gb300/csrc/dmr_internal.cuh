@@ -24,6 +24,9 @@ struct DevProblem {
   const void* plain[2];
   const void* cells[2];
   const uint8_t* cflag[2];
+  // per cell: bit (dz+1)*16 + (dy+1)*4 + (dx+1) set when voxel (i+dx, j+dy,
+  // k+dz) (clamped) is 0, for dx, dy, dz in -1..2
+  const unsigned long long* cmask[2];
   int n[2][3];
   double spd[2][3];
   float sp[2][3];
@@ -82,6 +85,9 @@ struct __align__(16) ItemRec {
   double Gd[3][3];  // FP64 map matrix (fused multiply-adds, a few ulps from the exact order)
 };
 
+// Kernels one launch_raster call launches (fast, full-logic).
+constexpr int kRasterLaunches = 2;
+
 // A batch of (trial, tet) pairs to evaluate.
 struct Batch {
   int n_tt;
@@ -100,7 +106,8 @@ struct Batch {
   int* o_cov;               // [n_tt][2]
   double* o_def;            // [n_tt]
   int* o_fold;              // [n_tt]
-  unsigned* work;           // raster work counter
+  unsigned* work;           // [3] raster counters: fast-kernel items taken, items handed over, handed-over items taken
+  int* slow;                // [2 n_tt] items the fast raster kernel hands to the full-logic kernel
   // partial-evaluation landmark outputs
   int aff_cap;
   int* aff_n;               // [n_trials]
@@ -113,13 +120,21 @@ struct Batch {
 
 // Kernel launchers (dmr_kernels.cu).  All enqueue on `st`.
 void launch_convert_image(const void* src, int src_dtype, void* dst, int dst_dtype, long n, cudaStream_t st);
-void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag, cudaStream_t st);
+void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag,
+                        unsigned long long* cmask, cudaStream_t st);
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
+// Raster kernels: fast pass, then the full-logic pass over the items it
+// handed over.  With a side stream, `fork` is recorded on `st` after the fast
+// pass and the side stream waits on it (work placed there runs beside the
+// full-logic pass).
 void launch_raster(const DevProblem* probs, const Batch& b, int storage_dtype, int warps, int vpw, int n_sm,
-                   cudaStream_t st);
-void launch_raster_f32(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st);
-void launch_raster_bf16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st);
-void launch_raster_f16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st);
+                   cudaStream_t st, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr);
+void launch_raster_f32(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st,
+                       cudaStream_t side, cudaEvent_t fork);
+void launch_raster_bf16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st,
+                        cudaStream_t side, cudaEvent_t fork);
+void launch_raster_f16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st,
+                       cudaStream_t side, cudaEvent_t fork);
 void launch_locate_full(const DevProblem* probs, const DevProblem& host_pr, const Batch& b, int c0, int nc,
                         cudaStream_t st);
 void launch_reduce_full(const DevProblem* probs, int c0, int nc, const Batch& b, double* obj, cudaStream_t st);

@@ -40,7 +40,8 @@ void launch_convert_image(const void* src, int sdt, void* dst, int ddt, long n, 
   k_convert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, sdt, dst, ddt, n);
 }
 
-__global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz, void* cells, uint8_t* cflag) {
+__global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz, void* cells, uint8_t* cflag,
+                              unsigned long long* cmask) {
   long Nx = nx + 2, Ny = ny + 2, Nz = nz + 2;
   long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (id >= Nx * Ny * Nz) return;
@@ -67,14 +68,20 @@ __global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz,
   // 4x4x4 voxel block (i-1 .. i+2 per axis, clamped): every support of a
   // sample whose FP32 cell is this one lies inside it
   int nb_all0 = 1, nb_none0 = 1;
+  unsigned long long zm = 0ull;
   for (int dz = -1; dz <= 2; ++dz)
     for (int dy = -1; dy <= 2; ++dy)
       for (int dx = -1; dx <= 2; ++dx) {
         int x = min(max(i + dx, 0), nx - 1), y = min(max(j + dy, 0), ny - 1), z = min(max(k + dz, 0), nz - 1);
         float v = load_plain_dyn(plain, st, ((long)z * ny + y) * nx + x);
-        if (v == 0.0f) nb_none0 = 0;
-        else nb_all0 = 0;
+        if (v == 0.0f) {
+          nb_none0 = 0;
+          zm |= 1ull << ((dz + 1) * 16 + (dy + 1) * 4 + (dx + 1));
+        } else {
+          nb_all0 = 0;
+        }
       }
+  cmask[id] = zm;
   if (st == ST_F32) {
     float4* p = (float4*)cells + 2 * id;
     p[0] = make_float4(fv[0], fv[1], fv[2], fv[3]);
@@ -90,9 +97,10 @@ __global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz,
   cflag[id] = (uint8_t)(any0 | (all0 << 1) | (nb_all0 << 2) | (nb_none0 << 3));
 }
 
-void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag, cudaStream_t st) {
+void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag,
+                        unsigned long long* cmask, cudaStream_t st) {
   long N = (long)(n[0] + 2) * (n[1] + 2) * (n[2] + 2);
-  k_build_cells<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(plain, dtype, n[0], n[1], n[2], cells, cflag);
+  k_build_cells<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(plain, dtype, n[0], n[1], n[2], cells, cflag, cmask);
 }
 
 // ------------------------------------------------------------ geometry set-up
@@ -116,15 +124,17 @@ __device__ __forceinline__ double edge6(const double (&E)[6][3], int i, int j, i
 }
 
 // v[i][a] for a runtime vertex index i without indexing local memory
-__device__ __forceinline__ float pick4(const float (&v)[4][3], int i, int a) {
+__device__ __forceinline__ double pick4d(const double (&v)[4][3], int i, int a) {
   return i == 0 ? v[0][a] : i == 1 ? v[1][a] : i == 2 ? v[2][a] : v[3][a];
 }
+
+
 
 // One thread per (trial, tet): fold count, deformation, and the two
 // direction records (Sec. 2.3.1-2.3.4).
 __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b) {
   int tt = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tt == 0 && b.work) *b.work = 0u;
+  if (tt == 0 && b.work) b.work[0] = b.work[1] = b.work[2] = 0u;
   if (tt >= b.n_tt) return;
   int k = b.tt_trial[tt];
   int t = b.tt_tet[tt];
@@ -322,25 +332,25 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
     R.b0[3] = R.b1[3] = R.O[3] = R.Op[3] = 0;
     if (R.b0[0] > R.b1[0] || R.b0[1] > R.b1[1] || R.b0[2] > R.b1[2]) flags = 0;
     R.flags = flags;
-    // own vertices relative to O: FP64 difference rounded once to FP32
-    float vr[4][3];
+    // own vertices relative to O (FP64 difference; FP32 copy for the slices)
+    double vd[4][3];
     float V = 0.f;
     for (int i = 0; i < 4; ++i) {
       for (int a = 0; a < 3; ++a) {
-        vr[i][a] = (float)dsub(own[i][a], (double)O[a]);
-        R.vr[i][a] = vr[i][a];
-        V = fmaxf(V, fabsf(vr[i][a]));
+        vd[i][a] = dsub(own[i][a], (double)O[a]);
+        R.vr[i][a] = (float)vd[i][a];
+        V = fmaxf(V, fabsf(R.vr[i][a]));
       }
       R.vr[i][3] = 0.f;
     }
     // faces: FP64 normals from the six edge vectors (fused cross products,
-    // within 2^-51 U W of the oracle's), rounded once to FP32; offset B from
-    // the FP32 relative vertex.  h(q) = A.q + B at a voxel q = p - O of the
-    // box (0 <= q < L) differs from the FP64 predicate by at most
-    //   eps (an (L + V) + 4 an V + 3 (an L + |B|)) + 1.5e-14 (U W + an)(L + V)
-    // (normal rounding over |q - a| <= L + V; vertex rounding and the FP32
-    // dot for B; the FP32 evaluation; the FP64 predicate's own rounding),
-    // eps = 2^-24 taken as 2^-22.
+    // within 2^-51 U W of the oracle's) and FP64 offsets B = -s n.(a - O),
+    // each rounded once to FP32.  At a voxel q = p - O of the box
+    // (0 <= q < L), h(q) = fl(A.q + B) differs from the FP64 predicate by at
+    // most eps (an L + |B|) from rounding A and B, plus 3 eps (an L + |B|)
+    // from the evaluation (eps = 2^-24), plus 1.5e-14 (U W + an)(L + V) for
+    // the FP64 predicate's own rounding.  The margin takes twice the FP32
+    // part: 2^-21 (an L + |B|).
     const double E6[6][3] = {{eo[0][0], eo[0][1], eo[0][2]},
                              {eo[1][0], eo[1][1], eo[1][2]},
                              {eo[2][0], eo[2][1], eo[2][2]},
@@ -349,7 +359,6 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
                              {dsub(own[3][0], own[2][0]), dsub(own[3][1], own[2][1]), dsub(own[3][2], own[2][2])}};
     const uint32_t fp = pr.fperm[t];
     const float Lf = (float)L;
-    const float e22 = 1.0f / 4194304.0f;
     for (int f = 0; f < 4; ++f) {
       const int ia = face_local(fp, f, 0), ib = face_local(fp, f, 1), ic = face_local(fp, f, 2);
       const double s = (double)face_sign(fp, f);
@@ -358,23 +367,21 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
         u[a] = edge6(E6, ia, ib, a);
         w[a] = edge6(E6, ia, ic, a);
       }
-      const float Ax = (float)(s * fma(u[1], w[2], -u[2] * w[1]));
-      const float Ay = (float)(s * fma(u[2], w[0], -u[0] * w[2]));
-      const float Az = (float)(s * fma(u[0], w[1], -u[1] * w[0]));
-      float va[3];
-      for (int a = 0; a < 3; ++a) va[a] = pick4(vr, ia, a);
-      const float Bp = -fmaf(Ax, va[0], fmaf(Ay, va[1], Az * va[2]));
+      const double nx = s * fma(u[1], w[2], -u[2] * w[1]);
+      const double ny = s * fma(u[2], w[0], -u[0] * w[2]);
+      const double nz = s * fma(u[0], w[1], -u[1] * w[0]);
+      const double Bd = -fma(nx, pick4d(vd, ia, 0), fma(ny, pick4d(vd, ia, 1), nz * pick4d(vd, ia, 2)));
+      const float Ax = (float)nx, Ay = (float)ny, Az = (float)nz, Bp = (float)Bd;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
       const float UW = fabs3max((float)u[0], (float)u[1], (float)u[2]) * fabs3max((float)w[0], (float)w[1], (float)w[2]);
-      const float mu = e22 * (an * (4.0f * Lf + 5.0f * V) + 3.0f * fabsf(Bp)) +
-                       1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
+      const float mu = (1.0f / 2097152.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
       R.fa[f][0] = Ax;
       R.fa[f][1] = Ay;
       R.fa[f][2] = Az;
       R.fa[f][3] = Bp;
       R.fm[f][0] = mu;
       R.fm[f][1] = 1.0f / Ax;
-      R.fm[f][2] = e22 * 4.0f * an + 1.5e-14f * (UW + an);
+      R.fm[f][2] = (1.0f / 2097152.0f) * an + 1.5e-14f * (UW + an);
       // bound on |A.x - s n_x| beyond FP32 rounding: the fused and the
       // oracle-order FP64 normals differ by a few 2^-53 U W
       R.fm[f][3] = 3.0e-14f * UW + 1e-30f;
@@ -431,11 +438,17 @@ void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st) {
 
 // ------------------------------------------------------------ raster + sample
 void launch_raster(const DevProblem* probs, const Batch& b, int st_dtype, int warps, int vpw, int n_sm,
-                   cudaStream_t st) {
-  if (b.n_tt <= 0) return;
-  if (st_dtype == ST_F32) launch_raster_f32(probs, b, warps, vpw, n_sm, st);
-  else if (st_dtype == ST_BF16) launch_raster_bf16(probs, b, warps, vpw, n_sm, st);
-  else launch_raster_f16(probs, b, warps, vpw, n_sm, st);
+                   cudaStream_t st, cudaStream_t side, cudaEvent_t fork) {
+  if (b.n_tt <= 0) {
+    if (side && fork) {
+      cudaEventRecord(fork, st);
+      cudaStreamWaitEvent(side, fork, 0);
+    }
+    return;
+  }
+  if (st_dtype == ST_F32) launch_raster_f32(probs, b, warps, vpw, n_sm, st, side, fork);
+  else if (st_dtype == ST_BF16) launch_raster_bf16(probs, b, warps, vpw, n_sm, st, side, fork);
+  else launch_raster_f16(probs, b, warps, vpw, n_sm, st, side, fork);
 }
 
 // ------------------------------------------------------------ landmarks

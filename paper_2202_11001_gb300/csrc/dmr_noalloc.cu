@@ -39,8 +39,9 @@ constexpr size_t kOffTrial = al(kOffTtTet + (size_t)kMaxTets * sizeof(int));   /
 constexpr size_t kOffLoc = al(kOffTrial + 3 * sizeof(int));
 constexpr size_t kOffGterm = al(kOffLoc + 2 * (size_t)kMaxGuide * sizeof(int));
 constexpr size_t kOffSums = al(kOffGterm + 2 * (size_t)kMaxGuide * sizeof(double));
-constexpr size_t kOffCount = al(kOffSums + 4 * sizeof(double));                // samples (u64), work (u32)
-constexpr size_t kScratchBytes = al(kOffCount + 16);
+constexpr size_t kOffSlow = al(kOffSums + 4 * sizeof(double));
+constexpr size_t kOffCount = al(kOffSlow + 2 * (size_t)kMaxTets * sizeof(int));  // samples (u64), work (3 x u32)
+constexpr size_t kScratchBytes = al(kOffCount + 24);
 
 // The scratch.  Host code must not pass this name to a kernel: on the host it
 // is only a stand-in; the device address comes from cudaGetSymbolAddress.
@@ -62,7 +63,7 @@ __global__ void k_noalloc_init(DevProblem hp, unsigned char* base, int ntet) {
     tr[1] = 0;     // first (trial, tet) pair
     tr[2] = ntet;  // all tets
     *(unsigned long long*)(base + kOffCount) = 0ull;
-    *(unsigned*)(base + kOffCount + 8) = 0u;
+    for (int k = 0; k < 3; ++k) ((unsigned*)(base + kOffCount + 8))[k] = 0u;
   }
   if (i < ntet) {
     ((int*)(base + kOffTtTrial))[i] = 0;
@@ -143,6 +144,7 @@ extern "C" int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double
   b.o_def = hp.c_def;
   b.o_fold = hp.c_fold;
   b.work = (unsigned*)(base + kOffCount + 8);
+  b.slow = (int*)(base + kOffSlow);
   k_noalloc_init<<<(hp.ntet + 255) / 256, 256, 0, st>>>(hp, base, hp.ntet);
   launch_setup(d_prob, b, st);
   launch_raster(d_prob, b, storage, warps, 32, n_sm, st);

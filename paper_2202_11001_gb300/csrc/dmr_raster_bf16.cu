@@ -3,8 +3,9 @@
 
 namespace dmr {
 
-void launch_raster_bf16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st) {
-  raster_launch<ST_BF16>(probs, b, warps, vpw, n_sm, st);
+void launch_raster_bf16(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st,
+                       cudaStream_t side, cudaEvent_t fork) {
+  raster_launch<ST_BF16>(probs, b, warps, vpw, n_sm, st, side, fork);
 }
 
 }  // namespace dmr
