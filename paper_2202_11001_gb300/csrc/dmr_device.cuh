@@ -453,8 +453,9 @@ enum { CF_ANY0 = 1, CF_ALL0 = 2, CF_NB_ALL0 = 4, CF_NB_NONE0 = 8 };
 // certify, or a sample whose black decision needs the FP64 definition, is
 // abandoned and appended to b.slow.  FAST = false: the same item logic with
 // the careful span and the exact black decision inline, over the items of
-// b.slow.  Which items are handed over depends only on the data, so results
-// do not depend on the tile shape.
+// b.slow, the WARPS warps of a CTA sharing one item (row batches dealt
+// round-robin, partial sums added in warp order).  Which items are handed
+// over depends only on the data, so results do not depend on the tile shape.
 template <int ST, int WARPS, int VPL, bool FAST>
 __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM / (WARPS * 32) > 0
                                                     ? DMR_RASTER_THREADS_PER_SM / (WARPS * 32)
@@ -463,28 +464,39 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem* ws = (WarpSmem*)smem_raw + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
   const unsigned lemask = 0xffffffffu >> (31 - lane);
   const int n_items = 2 * b.n_tt;
+  __shared__ int s_item;
+  __shared__ double s_part[WARPS];
+  __shared__ int s_cov[WARPS];
   for (;;) {
     int item = 0;
-    if (lane == 0) {
-      if constexpr (FAST) {
-        item = (int)atomicAdd(b.work, 1u);
-      } else {
+    if constexpr (FAST) {
+      if (lane == 0) item = (int)atomicAdd(b.work, 1u);
+      item = __shfl_sync(FULL_MASK, item, 0);
+    } else {
+      if (threadIdx.x == 0) {
         const unsigned w = atomicAdd(b.work + 2, 1u);
-        item = w < *(volatile unsigned*)(b.work + 1) ? b.slow[w] : n_items;
+        s_item = w < *(volatile unsigned*)(b.work + 1) ? b.slow[w] : n_items;
       }
+      __syncthreads();
+      item = s_item;
     }
-    item = __shfl_sync(FULL_MASK, item, 0);
     if (item >= n_items) break;
-    {
+    constexpr int NW = sizeof(ItemRec) / 16;
+    if constexpr (FAST) {
       const int4* src = (const int4*)(b.rec + item);
       int4* dst = (int4*)&ws->rec;
-      constexpr int NW = sizeof(ItemRec) / 16;
       for (int i = lane; i < NW; i += 32) dst[i] = __ldg(src + i);
+      __syncwarp();
+    } else {
+      const int4* src = (const int4*)(b.rec + item);
+      int4* dst = (int4*)&((WarpSmem*)smem_raw)->rec;
+      for (int i = threadIdx.x; i < NW; i += 32 * WARPS) dst[i] = __ldg(src + i);
+      __syncthreads();
     }
-    __syncwarp();
-    const ItemRec& r = ws->rec;
+    const ItemRec& r = FAST ? ws->rec : ((WarpSmem*)smem_raw)->rec;
     float sum = 0.f, comp = 0.f;
     int cov = 0;
     bool need_exact = false;  // FAST: some sample needs the FP64 black decision
@@ -519,7 +531,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
         const int yincl = warp_incl_scan(ycnt, lane);
         const int yexcl = yincl - ycnt;
         const int R = __shfl_sync(FULL_MASK, yincl, 31);
-        for (int rb = 0; rb < R; rb += 32) {
+        for (int rb = FAST ? 0 : 32 * wid; rb < R; rb += FAST ? 32 : 32 * WARPS) {
           const int rr = rb + lane;
           const bool has_row = rr < R;
           const int rq = has_row ? rr : R - 1;
@@ -692,12 +704,30 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
         lo = lo + ol + err;
       }
       const int covt = __reduce_add_sync(FULL_MASK, cov);
-      __syncwarp();
-      if (lane == 0) {
-        b.o_ssd[item] = (double)hi + (double)lo;
-        b.o_cov[item] = covt;
+      if constexpr (FAST) {
+        if (lane == 0) {
+          b.o_ssd[item] = (double)hi + (double)lo;
+          b.o_cov[item] = covt;
+        }
+        __syncwarp();
+      } else {
+        if (lane == 0) {
+          s_part[wid] = (double)hi + (double)lo;
+          s_cov[wid] = covt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double t = 0.0;
+          int c = 0;
+          for (int w = 0; w < WARPS; ++w) {
+            t += s_part[w];
+            c += s_cov[w];
+          }
+          b.o_ssd[item] = t;
+          b.o_cov[item] = c;
+        }
+        __syncthreads();
       }
-      __syncwarp();
     }
     continue;
   handover:

@@ -113,14 +113,14 @@ __device__ __forceinline__ double vcoord(const DevProblem& pr, const Batch& b, i
 
 __device__ __forceinline__ float fabs3max(float a, float b, float c) { return fmaxf(fabsf(a), fmaxf(fabsf(b), fabsf(c))); }
 
-// Edge vector X_j - X_i (i != j, local ids) from the six edges
-// E6 = {01, 02, 03, 12, 13, 23} (x - y = -(y - x) exactly), without
+// Edge vector X_j - X_i (i != j, local ids), negated if flip, from the six
+// edges E6 = {01, 02, 03, 12, 13, 23} (x - y = -(y - x) exactly), without
 // indexing local memory.
-__device__ __forceinline__ double edge6(const double (&E)[6][3], int i, int j, int a) {
+__device__ __forceinline__ double edge6(const double (&E)[6][3], int i, int j, int a, bool flip) {
   const int lo = min(i, j), hi = max(i, j);
   const int k = lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5);
   const double v = k == 0 ? E[0][a] : k == 1 ? E[1][a] : k == 2 ? E[2][a] : k == 3 ? E[3][a] : k == 4 ? E[4][a] : E[5][a];
-  return i < j ? v : -v;
+  return (i < j) != flip ? v : -v;
 }
 
 // v[i][a] for a runtime vertex index i without indexing local memory
@@ -235,6 +235,25 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
     def = (double)acc;
   }
 
+  // FP32 bounding boxes of both meshes' vertices (rounding is monotone, so
+  // ceil/floor of the rounded extremes give a superset of the voxels a tet
+  // can hold); finiteness of every rounded coordinate
+  float mlo[2][3], mhi[2][3];
+  bool mfin[2];
+  for (int mesh = 0; mesh < 2; ++mesh) {
+    mfin[mesh] = true;
+    for (int a = 0; a < 3; ++a) {
+      mlo[mesh][a] = mhi[mesh][a] = (float)X[mesh][0][a];
+      mfin[mesh] = mfin[mesh] && isfinite(mlo[mesh][a]);
+      for (int i = 1; i < 4; ++i) {
+        const float v = (float)X[mesh][i][a];
+        mlo[mesh][a] = fminf(mlo[mesh][a], v);
+        mhi[mesh][a] = fmaxf(mhi[mesh][a], v);
+        mfin[mesh] = mfin[mesh] && isfinite(v);
+      }
+    }
+  }
+
   // the two directions (unrolled so the vertex arrays stay in registers)
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
@@ -298,23 +317,12 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
       }
       continue;
     }
-    // bbox and origins in FP32: rounding is monotone, so ceil/floor of the
-    // rounded extremes give a superset of the voxels the tet can hold
-    float lo[3], hi[3], plo[3], phi[3];
-    bool pfin = true;
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = hi[a] = (float)own[0][a];
-      plo[a] = phi[a] = (float)par[0][a];
-      pfin = pfin && isfinite(plo[a]);
-      for (int i = 1; i < 4; ++i) {
-        const float v = (float)own[i][a], w = (float)par[i][a];
-        lo[a] = fminf(lo[a], v);
-        hi[a] = fmaxf(hi[a], v);
-        plo[a] = fminf(plo[a], w);
-        phi[a] = fmaxf(phi[a], w);
-        pfin = pfin && isfinite(w);
-      }
-    }
+    // bbox and origins
+    const float* lo = mlo[d];
+    const float* hi = mhi[d];
+    const float* plo = mlo[1 - d];
+    const float* phi = mhi[1 - d];
+    const bool pfin = mfin[1 - d];
     int O[3], Op[3];
     int L = 1;
     for (int a = 0; a < 3; ++a) {
@@ -359,21 +367,24 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
                              {dsub(own[3][0], own[2][0]), dsub(own[3][1], own[2][1]), dsub(own[3][2], own[2][2])}};
     const uint32_t fp = pr.fperm[t];
     const float Lf = (float)L;
+    // edge magnitudes are bounded by the box extent: |u|, |w| <= ext
+    const float ext = 1.001f * fmaxf(hi[0] - lo[0], fmaxf(hi[1] - lo[1], hi[2] - lo[2]));
+    const float UW = ext * ext;
     for (int f = 0; f < 4; ++f) {
       const int ia = face_local(fp, f, 0), ib = face_local(fp, f, 1), ic = face_local(fp, f, 2);
-      const double s = (double)face_sign(fp, f);
+      // inward sign folded into the first edge: s (u x w) = (s u) x w
+      const bool flip = face_sign(fp, f) < 0;
       double u[3], w[3];
       for (int a = 0; a < 3; ++a) {
-        u[a] = edge6(E6, ia, ib, a);
-        w[a] = edge6(E6, ia, ic, a);
+        u[a] = edge6(E6, ia, ib, a, flip);
+        w[a] = edge6(E6, ia, ic, a, false);
       }
-      const double nx = s * fma(u[1], w[2], -u[2] * w[1]);
-      const double ny = s * fma(u[2], w[0], -u[0] * w[2]);
-      const double nz = s * fma(u[0], w[1], -u[1] * w[0]);
+      const double nx = fma(u[1], w[2], -u[2] * w[1]);
+      const double ny = fma(u[2], w[0], -u[0] * w[2]);
+      const double nz = fma(u[0], w[1], -u[1] * w[0]);
       const double Bd = -fma(nx, pick4d(vd, ia, 0), fma(ny, pick4d(vd, ia, 1), nz * pick4d(vd, ia, 2)));
       const float Ax = (float)nx, Ay = (float)ny, Az = (float)nz, Bp = (float)Bd;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
-      const float UW = fabs3max((float)u[0], (float)u[1], (float)u[2]) * fabs3max((float)w[0], (float)w[1], (float)w[2]);
       const float mu = (1.0f / 2097152.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
       R.fa[f][0] = Ax;
       R.fa[f][1] = Ay;
@@ -612,7 +623,7 @@ __device__ __forceinline__ bool sorted_has(const int* tl, int n, int v) {
   return false;
 }
 
-__global__ void __launch_bounds__(32 * kLmWarps) k_landmarks_partial(const DevProblem* probs, Batch b) {
+__global__ void __launch_bounds__(32 * kLmWarps, 3) k_landmarks_partial(const DevProblem* probs, Batch b) {
   __shared__ int s_tl[kLmWarps][kLmTl];
   int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
