@@ -673,7 +673,6 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
                   if ((o == 0.0f) != blk) d2 = 1.0f;
                 }
                 bsum += d2;
-                ++cov;
               }
             }
             if constexpr (FAST) {
@@ -686,6 +685,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
             comp = (tk - sum) - yk;
             sum = tk;
           }
+          cov += T;  // every voxel of the batch's rows is one sample
           __syncwarp();
         }
       }
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
         hi = sh;
         lo = lo + ol + err;
       }
-      const int covt = __reduce_add_sync(FULL_MASK, cov);
+      const int covt = __shfl_sync(FULL_MASK, cov, 0);  // cov is warp-uniform
       if constexpr (FAST) {
         if (lane == 0) {
           b.o_ssd[item] = (double)hi + (double)lo;
