@@ -37,6 +37,24 @@ UNIT = "voxel-samples/s"
 # and square 2, black test 3, accumulate 1).
 ALG_OPS_PER_SAMPLE = 37
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) of one fast raster-pass launch (one wave of the
+# generation), from the ncu capture summarised in profiles/raster_fast_ellipsoid64.md;
+# None for workloads without a capture of the current kernel.
+FAST_PASS_DRAM_BYTES = {("ellipsoid64", "f32"): 88.3e6}
+
+
+def reduce_over_ranks(total_s, samples, dist, device):
+    """Whole-job figures over the replicas: the slowest rank's time and the
+    summed samples (each rank evaluates its own independent population)."""
+    if dist is None:
+        return float(total_s), float(samples)
+    import torch
+
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(samples)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
 
 
 def log(*a):
@@ -264,9 +282,10 @@ def measured_peaks():
     return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def cpu_baseline(pr, groups, waves, C, rng_seed, budget_s=20.0):
+def cpu_baseline(pr, groups, waves, C, rng_seed, min_s=10.0, max_s=30.0):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample:
-    partial evaluations of the first waves of the generation."""
+    partial evaluations of the generation's waves (repeated until about
+    min_s of work), then a single-thread timing on part of the first wave."""
     from oracle import oracle as orc
     from paper_2202_11001_gb300 import synth
 
@@ -276,24 +295,81 @@ def cpu_baseline(pr, groups, waves, C, rng_seed, budget_s=20.0):
     o = orc.Oracle(src, tgt, *pr["spacing"], pr["mesh"], guide=pr["guide"], model=orc.LINEAR)
     o.eval_full(pr["coords"])
     rng = np.random.default_rng(rng_seed)
-    samples, secs, nw, ntr = 0, 0.0, 0, 0
+    cur = np.stack([o.coords(c) for c in range(C)])
+    batches = []
     for w in waves:
         gids = np.repeat(w, C)
         cids = np.tile(np.arange(C), len(w))
-        cur = np.stack([o.coords(c) for c in range(C)])
         tc = synth.trial_coords(cur, groups, gids, cids, pr["sigma"], pr["mesh"], rng)
+        batches.append((gids, cids, tc))
+    samples, secs, nw, ntr, it = 0, 0.0, 0, 0, 0
+    cov_of = []
+    while secs < min_s and secs < max_s:
+        gids, cids, tc = batches[it % len(batches)]
         t0 = time.perf_counter()
         o.eval_partial(groups, gids, cids, tc)
         secs += time.perf_counter() - t0
-        for k in range(len(gids)):
-            samples += int(o.trial(k, cap=256)["cov"].sum())
+        if it < len(batches):
+            cov_of.append(sum(int(o.trial(k, cap=256)["cov"].sum()) for k in range(len(gids))))
+        samples += cov_of[it % len(batches)]
         nw += 1
         ntr += len(gids)
-        if secs >= budget_s:
-            break
-    return {"value": samples / secs, "unit": UNIT, "cores": orc.max_threads() if cores > 1 else 1,
-            "kind": "oracle", "sample": "%d of %d waves (%d trials, %d voxel-samples), FP64 C oracle, OpenMP over "
-                                         "trials, %.1f s" % (nw, len(waves), ntr, samples, secs)}
+        it += 1
+    value = samples / secs
+    # single thread: the first trials of the first wave
+    gids, cids, tc = batches[0]
+    n1 = min(len(gids), 400)
+    orc.set_threads(1)
+    t0 = time.perf_counter()
+    o.eval_partial(groups, gids[:n1], cids[:n1], tc[:n1])
+    s1 = time.perf_counter() - t0
+    c1 = sum(int(o.trial(k, cap=256)["cov"].sum()) for k in range(n1))
+    orc.set_threads(cores)
+    return {"value": value, "unit": UNIT, "cores": orc.max_threads() if cores > 1 else 1,
+            "kind": "oracle", "single_thread_value": c1 / s1,
+            "sample": "%d wave evaluations (%d of %d waves, repeated; %d trials, %d voxel-samples), FP64 C oracle, "
+                      "OpenMP over trials, %.1f s; single thread: %d trials of the first wave, %.1f s"
+                      % (nw, min(nw, len(waves)), len(waves), ntr, samples, secs, n1, s1)}
+
+
+def precision_report(pr, stream, n_cand=8):
+    """Objective errors of the reduced-precision image storage (Sec. 2.3.2
+    dissimilarity with FP32 sampling): against the oracle fed the same
+    quantised images (arithmetic error) and against the oracle fed the FP32
+    images (quantisation error); max relative error per objective over the
+    first n_cand candidates of a full evaluation."""
+    import torch
+    from oracle import oracle as orc
+    from paper_2202_11001_gb300 import dmr
+
+    orc.set_threads(os.cpu_count() or 1)
+    src, tgt = pr["img"]
+    coords = np.ascontiguousarray(pr["coords"][:n_cand])
+
+    def quant(img, st):
+        if st == "f32":
+            return np.asarray(img, np.float32)
+        dt = torch.bfloat16 if st == "bf16" else torch.float16
+        return torch.from_numpy(np.asarray(img, np.float32)).to(dt).to(torch.float32).numpy()
+
+    def oracle_obj(s_img, t_img):
+        o = orc.Oracle(s_img, t_img, *pr["spacing"], pr["mesh"], guide=pr["guide"], model=orc.LINEAR)
+        return np.asarray(o.eval_full(coords))
+
+    def rel(a, b):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        return [float(np.max(np.abs(a[:, q] - b[:, q]) / np.maximum(np.abs(b[:, q]), 1e-300))) for q in range(3)]
+
+    ref32 = oracle_obj(quant(src, "f32"), quant(tgt, "f32"))
+    out = {"objectives": ["f_sim", "f_def", "f_guid"], "candidates": n_cand}
+    for st in ("f32", "bf16", "f16"):
+        g = dmr.Problem(src, tgt, *pr["spacing"], pr["mesh"], guide=pr["guide"], model=dmr.LINEAR, storage=st,
+                        max_candidates=n_cand, stream=stream)
+        gpu = np.asarray(g.eval_full(coords))
+        g.close()
+        refq = ref32 if st == "f32" else oracle_obj(quant(src, st), quant(tgt, st))
+        out[st] = {"arith_rel_err": rel(gpu, refq), "quant_rel_err": rel(gpu, ref32)}
+    return out
 
 
 def run_reference(args):
@@ -430,14 +506,7 @@ def main():
     clocks = sampler.stop()
     samples = g.samples(reset=True)
     total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s, float(samples)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        total_s, all_samples = float(tmax[0]), float(t[1])
-    else:
-        all_samples = float(samples)
+    total_s, all_samples = reduce_over_ranks(total_s, samples, dist, "cuda")
     value = all_samples / total_s
     samples_per_step = samples / args.steps
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -477,8 +546,10 @@ def main():
     achieved = samples_per_step * ALG_OPS_PER_SAMPLE / raster_s_per_step / 1e12
     bpv = 4 if args.storage == "f32" else 2
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    traffic = FAST_PASS_DRAM_BYTES.get((args.workload, args.storage))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-op/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per fast raster-pass launch (one wave), ncu",
                 "kernel": "k_raster (rasterise + map + trilinear sample + SSD)",
                 "ops_per_sample": ALG_OPS_PER_SAMPLE,
                 "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clock_max),
@@ -511,6 +582,10 @@ def main():
             pv.close()
             gv.close()
 
+    precision = None
+    if not args.no_variants and rank == 0 and world == 1 and args.workload != "ct":
+        precision = precision_report(pr, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pr, groups, waves, C, 7)
@@ -528,7 +603,8 @@ def main():
                            "l2": "flushed before every timed step (256 MiB write outside the event bracket)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": plan.launches * args.steps, "variants_samples_per_s": variants}
+                "gpu_launches": plan.launches * args.steps, "variants_samples_per_s": variants,
+                "precision": precision}
         print(json.dumps(line), flush=True)
     plan.close()
     g.close()
