@@ -206,6 +206,43 @@ def run_learned(args):
     return 0
 
 
+def run_mlp_forward(args):
+    """--workload mlp_forward: the fused tensor-core forward of the learned
+    proposal network over one generation's rows (population 512 x 1000 points
+    of the ct64 coarse level), features gathered on the GPU beforehand."""
+    import torch
+
+    from paper_2202_11001_gb300 import dmr, learned, synth
+
+    pr = synth.ct_phantom(seed=3, C=512, level="coarse")
+    net = dmr.MLP(seed=1)
+    prob = learned.make_problem(pr)
+    Xi = dmr.MLP.features(prob, torch.from_numpy(pr["coords"]).cuda())
+    for _ in range(args.warmup):
+        net.forward(Xi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        net.forward(Xi)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    rows = Xi.shape[0]
+    flop = rows * 2.0 * (256 * 128 + 128 * 128 * 2 + 128 * 16)
+    peaks, kind = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0)) if kind == "measured" else 1900.0
+    line = {"metric": "fused MLP forward throughput", "value": flop / ms / 1e9, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic (ct64 coarse features)",
+            "config": {"workload": "learned-proposal forward, %d rows x 256 features" % rows},
+            "roofline": {"bound": "tensor", "achieved": flop / ms / 1e9, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flop / ms / 1e9 / peak, "traffic": None, "peak_kind": kind},
+            "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def deltas_for(pr, groups, C, rng):
     from paper_2202_11001_gb300 import synth
 
@@ -443,6 +480,8 @@ def main():
         return run_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "mlp_forward":
+        return run_mlp_forward(args)
 
     import torch
 

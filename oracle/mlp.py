@@ -2,7 +2,9 @@
 
 Network: x [256] -> Linear(256,128) -> GELU -> Linear(128,128) -> GELU ->
 Linear(128,128) -> GELU -> Linear(128,6) -> (mean [3], log-variance [3]).
-GELU(z) = z * Phi(z) = 0.5 z (1 + erf(z / sqrt 2)).
+GELU in its tanh form (Hendrycks & Gimpel, "Gaussian Error Linear Units"):
+GELU(z) = 0.5 z (1 + tanh(c (z + a z^3))), c = sqrt(2 / pi), a = 0.044715,
+which stays within 1e-3 of z * Phi(z).
 Loss (Gaussian negative log-likelihood, constant dropped, mean over rows):
 L = 1/B sum_rows sum_d 0.5 ((y_d - mu_d)^2 exp(-s_d) + s_d).
 Adam: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
@@ -21,7 +23,8 @@ SHAPES = [("W1", (HID, IN)), ("b1", (HID,)), ("W2", (HID, HID)), ("b2", (HID,)),
           ("b3", (HID,)), ("W4", (OUTP, HID)), ("b4", (OUTP,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
 
-_erf = np.vectorize(math.erf)
+_C = math.sqrt(2.0 / math.pi)
+_A = 0.044715
 
 
 def unpack(flat):
@@ -38,11 +41,12 @@ def pack(d):
 
 
 def gelu(z):
-    return 0.5 * z * (1.0 + _erf(z / math.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(_C * (z + _A * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    t = np.tanh(_C * (z + _A * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * _C * (1.0 + 3.0 * _A * z * z)
 
 
 def forward(params, X):

@@ -1,6 +1,6 @@
 // Learned proposal network on the 5th-generation tensor cores (sm_103a).
 //
-// A small MLP (256 -> 128 -> 128 -> 128 -> 6, GELU) proposes a Gaussian
+// A small MLP (256 -> 128 -> 128 -> 128 -> 6, tanh-form GELU) proposes a Gaussian
 // displacement for every (candidate, point) of the target mesh; RV-GOMEA
 // mixes its samples into its own proposals.  The paper has no learned part;
 // this is the one dense contraction of the path, so it runs as tcgen05.mma
@@ -136,9 +136,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU in its tanh form (Hendrycks & Gimpel): 0.5 z (1 + tanh(c (z + a z^3))),
+// c = sqrt(2/pi), a = 0.044715; tanh from the hardware approximation, whose
+// error is below the BF16 rounding the activations receive.
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kGeluC = 0.7978845608028654f, kGeluA = 0.044715f;
+__device__ __forceinline__ float gelu(float z) {
+  const float t = tanh_hw(kGeluC * fmaf(kGeluA * z, z * z, z));
+  return 0.5f * z * (1.0f + t);
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
+  const float t = tanh_hw(kGeluC * fmaf(kGeluA * z, z * z, z));
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * kGeluC * fmaf(3.0f * kGeluA, z * z, 1.0f);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -165,7 +178,12 @@ struct FwdSmem {
                             MBAR = BIAS + (3 * kHid + kOutP) * 4, SLOT = MBAR + 8, TOTAL = SLOT + 8;
 };
 
-__global__ void __launch_bounds__(128, 1)
+// 16 warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and
+// accumulator columns 32 (w / 4) .. + 31, so the bias + GELU epilogue of a
+// 128 x 128 layer is spread over the whole CTA.
+constexpr int kFwdThreads = 512;
+
+__global__ void __launch_bounds__(kFwdThreads, 1)
     k_mlp_forward(const __nv_bfloat16* __restrict__ X, int n, const __nv_bfloat16* __restrict__ Wb,
                   const float* __restrict__ P, float* __restrict__ out, float* __restrict__ Zs,
                   __nv_bfloat16* __restrict__ Hs, int* err) {
@@ -180,7 +198,7 @@ __global__ void __launch_bounds__(128, 1)
   stage_weights(sm + FwdSmem::W2, Wb + kOffW2, kHid, kHid);
   stage_weights(sm + FwdSmem::W3, Wb + kOffW3, kHid, kHid);
   stage_weights(sm + FwdSmem::W4, Wb + kOffW4, kOutP, kHid);
-  for (int i = tid; i < kHid; i += 128) {
+  for (int i = tid; i < kHid; i += kFwdThreads) {
     bias[i] = P[kOffB1 + i];
     bias[kHid + i] = P[kOffB2 + i];
     bias[2 * kHid + i] = P[kOffB3 + i];
@@ -193,14 +211,15 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t sAct = smem_u32(sm + FwdSmem::ACT);
   const uint32_t sW[4] = {smem_u32(sm + FwdSmem::W1), smem_u32(sm + FwdSmem::W2), smem_u32(sm + FwdSmem::W3),
                           smem_u32(sm + FwdSmem::W4)};
-  const uint32_t lane_base = tbase + ((uint32_t)(32 * warp) << 16);
+  const int quarter = warp & 3, cgrp = warp >> 2;
+  const uint32_t lane_base = tbase + ((uint32_t)(32 * quarter) << 16);
   uint32_t phase = 0;
   bool ok = true;
   const int tiles = (n + 127) / 128;
   for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
     const int m0 = tile * 128;
     // stage the input tile (rows beyond n are zero)
-    for (int e = tid; e < 128 * (kIn / 8); e += 128) {
+    for (int e = tid; e < 128 * (kIn / 8); e += kFwdThreads) {
       int r = e / (kIn / 8), c = e % (kIn / 8);
       uint4 v = make_uint4(0, 0, 0, 0);
       if (m0 + r < n) v = *reinterpret_cast<const uint4*>(X + (size_t)(m0 + r) * kIn + c * 8);
@@ -225,11 +244,12 @@ __global__ void __launch_bounds__(128, 1)
       ok = __syncthreads_and(w) != 0;
       if (!ok) break;
       tc_fence_after();
-      const int row = 32 * warp + lane;
+      const int row = 32 * quarter + lane;
       const int grow = m0 + row;
       if (layer < 3) {
         // bias + GELU -> next layer's A operand (K = 128) in shared memory
-        for (int c0 = 0; c0 < kHid; c0 += 32) {
+        {
+          const int c0 = 32 * cgrp;
           float v[32];
           tmem_ld32(lane_base + (uint32_t)c0, v);
 #pragma unroll
@@ -247,7 +267,7 @@ __global__ void __launch_bounds__(128, 1)
               *reinterpret_cast<uint4*>(Hs + ((size_t)layer * n + grow) * kHid + c0 + 8 * q) = pk;
           }
         }
-      } else {
+      } else if (cgrp == 0) {
         float v[16];
         tmem_ld16(lane_base, v);
         if (grow < n)
@@ -528,7 +548,7 @@ void launch_forward(dmr_mlp* M, const __nv_bfloat16* X, int n, float* out, float
   }
   int tiles = (n + 127) / 128;
   int grid = std::min(tiles, M->n_sm);
-  k_mlp_forward<<<grid, 128, FwdSmem::TOTAL, M->st>>>(X, n, M->Wb, M->P, out, Zs, Hs, M->err);
+  k_mlp_forward<<<grid, kFwdThreads, FwdSmem::TOTAL, M->st>>>(X, n, M->Wb, M->P, out, Zs, Hs, M->err);
 }
 
 // SplitMix64, a published counter-based generator, for the initial weights.
