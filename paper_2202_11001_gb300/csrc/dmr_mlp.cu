@@ -159,6 +159,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// Asynchronous 16-byte global -> shared copy (zero fill when !valid).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Load R x K BF16 weights [R][K] from global into the canonical layout.
 __device__ void stage_weights(unsigned char* dst, const __nv_bfloat16* W, int R, int K) {
   const int chunks = R * (K / 8);
@@ -216,15 +223,29 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   uint32_t phase = 0;
   bool ok = true;
   const int tiles = (n + 127) / 128;
+  // Input tile staging, asynchronous and in two row halves: in the K = 256
+  // layout rows 64..127 occupy bytes 32K..64K of ACT, which layers 2..4 (K =
+  // 128 activations, bytes 0..32K) leave free, and rows 0..63 are free again
+  // once layer 4's MMA has read the layer-3 activations; so the next tile's
+  // halves load while this tile's layers run.  Rows beyond n are zero.
+  auto stage_half = [&](int t, int half) {
+    const int m0 = t * 128;
+    for (int e = tid; e < 64 * (kIn / 8); e += kFwdThreads) {
+      const int r = 64 * half + e / (kIn / 8), c = e % (kIn / 8);
+      const bool valid = m0 + r < n;
+      cp_async16(sAct + kmaj_off(r, c * 8, kIn), valid ? (const void*)(X + (size_t)(m0 + r) * kIn + c * 8) : (const void*)X,
+                 valid);
+    }
+    cp_async_commit();
+  };
+  if ((int)blockIdx.x < tiles) {
+    stage_half(blockIdx.x, 0);
+    stage_half(blockIdx.x, 1);
+  }
   for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
     const int m0 = tile * 128;
-    // stage the input tile (rows beyond n are zero)
-    for (int e = tid; e < 128 * (kIn / 8); e += kFwdThreads) {
-      int r = e / (kIn / 8), c = e % (kIn / 8);
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (m0 + r < n) v = *reinterpret_cast<const uint4*>(X + (size_t)(m0 + r) * kIn + c * 8);
-      *reinterpret_cast<uint4*>(sm + FwdSmem::ACT + kmaj_off(r, c * 8, kIn)) = v;
-    }
+    const int next = tile + gridDim.x;
+    cp_async_wait_all();
     for (int layer = 0; layer < 4 && ok; ++layer) {
       const int K = layer == 0 ? kIn : kHid;
       const int N = layer == 3 ? kOutP : kHid;
@@ -244,6 +265,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       ok = __syncthreads_and(w) != 0;
       if (!ok) break;
       tc_fence_after();
+      // the MMA has read its A operand: refill the half the next layers leave free
+      if (next < tiles && layer == 0) stage_half(next, 1);
+      if (next < tiles && layer == 3) stage_half(next, 0);
       const int row = 32 * quarter + lane;
       const int grow = m0 + row;
       if (layer < 3) {
@@ -280,6 +304,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     if (tid == 0) atomicExch(err, kErrTimeout);
     (void)mbar_wait(mbar, phase ^ 1u);  // give an outstanding commit one more bounded chance
   }
+  cp_async_wait_all();  // no copy in flight when the CTA leaves
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
