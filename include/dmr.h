@@ -222,6 +222,19 @@ int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, flo
  * enqueued on the problem's stream; the call does not wait for it. */
 int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double* obj_out);
 
+/* Grid refinement for the multi-resolution scheme (Sec. 2.4): every cube
+ * cell of both meshes gains a point in the middle of each edge, in the
+ * middle of each face and at its centre, so m[a] points per axis become
+ * 2 m[a] - 1.  A fine point on a coarse point copies it; otherwise it is the
+ * mean of the 2, 4 or 8 coarse corners of the edge, face or cube it lies in
+ * (summed in halves along the odd axes in z, y, x order, then scaled by
+ * 1/2, 1/4 or 1/8), so border coordinates stay exactly on their planes.
+ * coarse [n_cand][2][3][m0 m1 m2] and fine [n_cand][2][3][M0 M1 M2] FP64,
+ * host or device memory, caller-owned; m[a] >= 2.  Runs on `stream` (a
+ * cudaStream_t, 0 = the default stream) and returns after the result is in
+ * `fine`.  DMR_EINVAL for bad sizes or null pointers. */
+int dmr_refine(const double* coarse, int n_cand, const int* m, double* fine, void* stream);
+
 /* Exact hypervolume (host code, no GPU): the measure of the union of the
  * boxes [p_i, ref] of n points of dimension d (1..6, minimisation), the
  * quality score of an approximation set (Sec. 1; the elitist archive of

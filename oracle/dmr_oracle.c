@@ -1045,3 +1045,48 @@ double dmo_six_vol(void* h, int mesh, const double* coords, int t) {
   tet_vertices(pr, coords, mesh, t, X);
   return six_vol(X);
 }
+
+/* ------------------------------------------------------------------ refinement
+ * Grid multi-resolution (Sec. 2.4): every cube cell of both meshes gains a
+ * point in the middle of each edge, in the middle of each face and at its
+ * centre, so m points per axis become 2m - 1.  Fine point (A, B, C) sits on
+ * coarse point (A/2, B/2, C/2) when all its indices are even; otherwise it is
+ * the mean of the coarse points at the corners of the edge, face or cube it
+ * lies in (a deformed face is non-planar: the mean of its 4 corners; the
+ * cube's centre of mass: the mean of its 8 corners).  Summation order, which
+ * the GPU follows as well: recursive halves along the odd axes taken in the
+ * order z, y, x, i.e. ((c_000 + c_001) + (c_010 + c_011)) + (...), then one
+ * exact scaling by 2^-k for k odd axes.
+ * coarse: [ncand][2][3][mx*my*mz]; fine: [ncand][2][3][Mx*My*Mz]. */
+static double refine_sum(const double* v, const int* m, int A, int B, int Cz, int level) {
+  /* level 0: z, 1: y, 2: x; recurse on odd fine indices */
+  const int idx[3] = {A, B, Cz};
+  if (level == 3) return v[(A / 2) + m[0] * ((B / 2) + m[1] * (Cz / 2))];
+  int ax = 2 - level; /* z first, then y, then x */
+  if (idx[ax] & 1) {
+    int lo[3] = {A, B, Cz}, hi[3] = {A, B, Cz};
+    lo[ax] -= 1;
+    hi[ax] += 1;
+    return refine_sum(v, m, lo[0], lo[1], lo[2], level + 1) + refine_sum(v, m, hi[0], hi[1], hi[2], level + 1);
+  }
+  return refine_sum(v, m, A, B, Cz, level + 1);
+}
+
+int dmo_refine(const double* coarse, int ncand, int mx, int my, int mz, double* fine) {
+  if (ncand < 0 || mx < 2 || my < 2 || mz < 2) return -1;
+  const int m[3] = {mx, my, mz};
+  const int M[3] = {2 * mx - 1, 2 * my - 1, 2 * mz - 1};
+  const long P = (long)mx * my * mz, PF = (long)M[0] * M[1] * M[2];
+  for (long cma = 0; cma < (long)ncand * 6; ++cma) {
+    const double* v = coarse + cma * P;
+    double* out = fine + cma * PF;
+    for (int Cz = 0; Cz < M[2]; ++Cz)
+      for (int B = 0; B < M[1]; ++B)
+        for (int A = 0; A < M[0]; ++A) {
+          int k = (A & 1) + (B & 1) + (Cz & 1);
+          double s = refine_sum(v, m, A, B, Cz, 0);
+          out[A + (long)M[0] * (B + (long)M[1] * Cz)] = s * (k == 0 ? 1.0 : k == 1 ? 0.5 : k == 2 ? 0.25 : 0.125);
+        }
+  }
+  return 0;
+}

@@ -81,6 +81,8 @@ def _load():
         lib.dmo_sample.argtypes = [vp, ctypes.c_int, _f64p, ctypes.POINTER(ctypes.c_int32)]
         lib.dmo_six_vol.restype = ctypes.c_double
         lib.dmo_six_vol.argtypes = [vp, ctypes.c_int, _f64p, ctypes.c_int]
+        lib.dmo_refine.restype = ctypes.c_int
+        lib.dmo_refine.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p]
         lib.dmo_num_tets.argtypes = [_i32p]
         lib.dmo_build_tets.argtypes = [_i32p, _i32p]
         lib.dmo_set_threads.argtypes = [ctypes.c_int]
@@ -280,6 +282,19 @@ class Oracle:
 
     def six_vol(self, mesh, coords1, t):
         return float(self._lib.dmo_six_vol(self.h, int(mesh), _f64(coords1).reshape(-1), int(t)))
+
+
+def refine(coarse, m):
+    """Grid refinement (Sec. 2.4): coords [C][2][3][P] on m points per axis ->
+    [C][2][3][P'] on 2m - 1 points per axis (edge, face and cube midpoints)."""
+    coarse = np.ascontiguousarray(coarse, np.float64)
+    C = coarse.shape[0]
+    M = [2 * int(a) - 1 for a in m]
+    fine = np.zeros((C, 2, 3, M[0] * M[1] * M[2]), np.float64)
+    rc = _load().dmo_refine(coarse.reshape(-1), C, int(m[0]), int(m[1]), int(m[2]), fine.reshape(-1))
+    if rc != 0:
+        raise ValueError("refine: bad arguments")
+    return fine
 
 
 def hypervolume_bruteforce(points, ref):

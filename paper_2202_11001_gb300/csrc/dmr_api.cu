@@ -989,6 +989,42 @@ int dmr_trial_out(dmr_problem* p, int k, int* tets, int* cov, double* ssd, doubl
   return n;
 }
 
+int dmr_refine(const double* coarse, int n_cand, const int* m, double* fine, void* stream) {
+  if (!coarse || !fine || !m || n_cand < 0) return fail(DMR_EINVAL, "refine: null argument");
+  for (int a = 0; a < 3; ++a)
+    if (m[a] < 2 || m[a] > 1024) return fail(DMR_EINVAL, "refine: points per axis out of range");
+  if (n_cand == 0) return DMR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)m[0] * m[1] * m[2];
+  const size_t PF = (size_t)(2 * m[0] - 1) * (2 * m[1] - 1) * (2 * m[2] - 1);
+  const size_t nc = (size_t)n_cand * 6 * P, nf = (size_t)n_cand * 6 * PF;
+  const double* dc = coarse;
+  double* df = fine;
+  double *tc = nullptr, *tf = nullptr;
+  int rc = DMR_OK;
+  if (!is_device_ptr(coarse)) {
+    if ((rc = dalloc(&tc, nc))) return rc;
+    cudaMemcpyAsync(tc, coarse, sizeof(double) * nc, cudaMemcpyHostToDevice, st);
+    dc = tc;
+  }
+  const bool host_out = !is_device_ptr(fine);
+  if (host_out) {
+    if ((rc = dalloc(&tf, nf))) {
+      dfree(tc);
+      return rc;
+    }
+    df = tf;
+  }
+  launch_refine(dc, n_cand, m, df, st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && host_out) e = cudaMemcpyAsync(fine, tf, sizeof(double) * nf, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(tc);
+  dfree(tf);
+  if (e != cudaSuccess) return fail(DMR_ECUDA, std::string("refine: ") + cudaGetErrorString(e));
+  return DMR_OK;
+}
+
 int dmr_samples(dmr_problem* p, long long* samples, int reset) {
   if (!p || !samples) return fail(DMR_EINVAL, "null argument");
   unsigned long long v = 0;

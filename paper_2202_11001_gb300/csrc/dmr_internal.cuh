@@ -123,6 +123,7 @@ void launch_convert_image(const void* src, int src_dtype, void* dst, int dst_dty
 void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag,
                         unsigned long long* cmask, cudaStream_t st);
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
+void launch_refine(const double* coarse, int n_cand, const int m[3], double* fine, cudaStream_t st);
 // Raster kernels: fast pass, then the full-logic pass over the items it
 // handed over.  With a side stream, `fork` is recorded on `st` after the fast
 // pass and the side stream waits on it (work placed there runs beside the

@@ -442,6 +442,55 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
   b.o_def[tt] = def;
 }
 
+// ------------------------------------------------------------ refinement
+// Grid multi-resolution (Sec. 2.4): one thread per (candidate, mesh, axis,
+// fine point).  The corners of the fine point's edge / face / cube are summed
+// in halves along its odd axes in z, y, x order, then scaled exactly.
+struct RefineDims {
+  int m[3], M[3];
+  long P, PF;
+};
+
+__device__ double refine_corner_sum(const double* v, const RefineDims& d, int A, int B, int C) {
+  // up to 8 corners; iterate the odd axes z, y, x as the binary digits of j
+  const int oz = C & 1, oy = B & 1, ox = A & 1;
+  double s[8];
+  int n = 0;
+  for (int jz = 0; jz <= oz; ++jz)
+    for (int jy = 0; jy <= oy; ++jy)
+      for (int jx = 0; jx <= ox; ++jx) {
+        const int a = (A - ox) / 2 + jx, b = (B - oy) / 2 + jy, c = (C - oz) / 2 + jz;
+        s[n++] = v[a + (long)d.m[0] * (b + (long)d.m[1] * c)];
+      }
+  // pairwise halves: the last odd axis (x) pairs neighbours first
+  for (int w = 1; w < n; w <<= 1)
+    for (int i = 0; i + w < n; i += 2 * w) s[i] = dadd(s[i], s[i + w]);
+  return s[0];
+}
+
+__global__ void k_refine(const double* __restrict__ coarse, int n_cand, RefineDims d, double* __restrict__ fine) {
+  const long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (id >= (long)n_cand * 6 * d.PF) return;
+  const long cma = id / d.PF, q = id % d.PF;
+  const int A = (int)(q % d.M[0]), B = (int)((q / d.M[0]) % d.M[1]), C = (int)(q / ((long)d.M[0] * d.M[1]));
+  const int k = (A & 1) + (B & 1) + (C & 1);
+  const double s = refine_corner_sum(coarse + cma * d.P, d, A, B, C);
+  fine[id] = dmul(s, k == 0 ? 1.0 : k == 1 ? 0.5 : k == 2 ? 0.25 : 0.125);
+}
+
+void launch_refine(const double* coarse, int n_cand, const int m[3], double* fine, cudaStream_t st) {
+  RefineDims d;
+  for (int a = 0; a < 3; ++a) {
+    d.m[a] = m[a];
+    d.M[a] = 2 * m[a] - 1;
+  }
+  d.P = (long)m[0] * m[1] * m[2];
+  d.PF = (long)d.M[0] * d.M[1] * d.M[2];
+  const long n = (long)n_cand * 6 * d.PF;
+  if (n <= 0) return;
+  k_refine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(coarse, n_cand, d, fine);
+}
+
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st) {
   if (b.n_tt <= 0) return;
   k_setup<<<(b.n_tt + 127) / 128, 128, 0, st>>>(probs, b);

@@ -89,6 +89,7 @@ def load():
         "dmr_batch_destroy": [vp],
         "dmr_batch_plan_generation": [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_hypervolume": [vp, i, i, vp, vp],
+        "dmr_refine": [vp, i, vp, vp, vp],
         "dmr_mlp_create": [ctypes.c_ulonglong, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_mlp_destroy": [vp],
         "dmr_mlp_n_params": [],
@@ -115,7 +116,7 @@ def exported_symbols():
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
         "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_batch_create", "dmr_batch_destroy",
-        "dmr_batch_plan_generation", "dmr_hypervolume", "dmr_mlp_create", "dmr_mlp_destroy", "dmr_mlp_n_params",
+        "dmr_batch_plan_generation", "dmr_hypervolume", "dmr_refine", "dmr_mlp_create", "dmr_mlp_destroy", "dmr_mlp_n_params",
         "dmr_mlp_params", "dmr_mlp_features", "dmr_mlp_forward", "dmr_mlp_train_step", "dmr_eval_one_noalloc", "dmr_last_error",
     ]
 
@@ -189,6 +190,28 @@ def hypervolume(points, ref):
     _check(lib.dmr_hypervolume(pts.ctypes.data if len(pts) else None, len(pts), len(r), r.ctypes.data,
                                ctypes.addressof(out)))
     return out.value
+
+
+def refine(coarse, m, stream=None):
+    """Grid refinement (Sec. 2.4): coords [C, 2, 3, P] on m points per axis ->
+    [C, 2, 3, P'] on 2m - 1 points per axis, computed on the GPU.  numpy in,
+    numpy out; a torch tensor in gives a torch tensor on the same device."""
+    lib = load()
+    M = [2 * int(a) - 1 for a in m]
+    C = int(coarse.shape[0])
+    mm = (ctypes.c_int * 3)(*[int(a) for a in m])
+    if _is_torch(coarse):
+        import torch
+
+        src = coarse.contiguous().to(torch.float64)
+        out = torch.empty((C, 2, 3, M[0] * M[1] * M[2]), dtype=torch.float64, device=src.device)
+        st = stream if stream is not None else (torch.cuda.current_stream().cuda_stream if src.is_cuda else 0)
+        _check(lib.dmr_refine(src.data_ptr(), C, ctypes.addressof(mm), out.data_ptr(), st))
+        return out
+    src = np.ascontiguousarray(coarse, np.float64)
+    out = np.zeros((C, 2, 3, M[0] * M[1] * M[2]), np.float64)
+    _check(lib.dmr_refine(src.ctypes.data, C, ctypes.addressof(mm), out.ctypes.data, stream or 0))
+    return out
 
 
 class Problem:

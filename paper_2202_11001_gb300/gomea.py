@@ -44,24 +44,35 @@ class Archive:
         self.coords = []
 
     def update(self, objs, coords_of):
-        new_o, new_c = [], []
-        for c in np.nonzero(objs[:, 3] == 0)[0]:
-            o = objs[c, :3]
-            if any(np.array_equal(o, x) for x in self.objs) or any(np.array_equal(o, x) for x in new_o):
-                continue
-            new_o.append(o)
-            new_c.append(int(c))
-        if not new_o:
+        """Add the feasible, mutually non-dominated candidates of objs [C, 4]
+        (exact duplicates of archive members are skipped) and drop archive
+        members they dominate."""
+        cand = np.nonzero(objs[:, 3] == 0)[0]
+        if len(cand) == 0:
             return
-        n_old = len(self.objs)
-        allo = np.vstack([self.objs, np.array(new_o)])
-        keep = nondominated(allo)
-        coords = list(self.coords) + [None] * len(new_o)
-        for j, c in enumerate(new_c):
-            if keep[n_old + j]:
-                coords[n_old + j] = coords_of(c)
-        self.objs = allo[keep]
-        self.coords = [coords[i] for i in np.nonzero(keep)[0]]
+        N = objs[cand, :3]
+        # exact duplicates (against the archive and among the candidates)
+        rows = np.ascontiguousarray(N).view(np.dtype((np.void, N.dtype.itemsize * 3))).ravel()
+        _, first = np.unique(rows, return_index=True)
+        keep = np.zeros(len(cand), bool)
+        keep[first] = True
+        if len(self.objs):
+            arows = np.ascontiguousarray(self.objs).view(np.dtype((np.void, N.dtype.itemsize * 3))).ravel()
+            keep &= ~np.isin(rows, arows)
+        cand, N = cand[keep], N[keep]
+        if len(cand) == 0:
+            return
+
+        def dominates(a, b):  # [i, j]: a_i dominates b_j
+            return np.all(a[:, None, :] <= b[None, :, :], axis=2) & np.any(a[:, None, :] < b[None, :, :], axis=2)
+
+        new_ok = ~np.any(dominates(N, N), axis=0)
+        old_ok = np.ones(len(self.objs), bool)
+        if len(self.objs):
+            new_ok &= ~np.any(dominates(self.objs, N), axis=0)
+            old_ok = ~np.any(dominates(N[new_ok], self.objs), axis=0)
+        self.objs = np.vstack([self.objs[old_ok], N[new_ok]])
+        self.coords = [c for c, k in zip(self.coords, old_ok) if k] + [coords_of(int(c)) for c in cand[new_ok]]
         if len(self.objs) > self.cap:
             idx = np.random.default_rng(0).choice(len(self.objs), self.cap, replace=False)
             self.objs = self.objs[idx]
@@ -74,7 +85,7 @@ class Archive:
 class Gomea:
     def __init__(self, prob, coords0, groups, mesh, sigma0, rng, proposal=None, alpha=0.25):
         self.prob = prob
-        self.mesh = mesh
+        self.mesh = tuple(mesh)
         self.groups = groups
         self.rng = rng
         self.C = coords0.shape[0]
@@ -168,3 +179,44 @@ class Gomea:
             self.generation()
             hv.append((self.evals, self.archive.hypervolume(ref)))
         return hv
+
+
+def seed_from_archive(archive, n, rng):
+    """Sec. 2.4: a finer-resolution run starts from a random sample, of its
+    population size, of the coarser run's approximation set (drawn with
+    replacement only when the set is smaller than the population)."""
+    k = len(archive.coords)
+    if k == 0:
+        raise ValueError("empty approximation set")
+    idx = rng.choice(k, size=n, replace=k < n)
+    return np.stack([archive.coords[i] for i in idx])
+
+
+def multi_resolution(build, coords0, levels, ref, rng):
+    """Grid multi-resolution run (Sec. 2.4): level 0 starts from coords0; each
+    next level refines a random sample of the previous level's approximation
+    set (edge, face and cube midpoints on the GPU, dmr.refine) and continues
+    from it.  build(mesh, C) -> a dmr.Problem for that mesh and population;
+    levels: [{"mesh", "C", "generations", "sigma0"}].  Returns per level the
+    hypervolume curve, the final archive and the feasible fraction of the
+    refined seeds."""
+    out = []
+    coords = np.asarray(coords0, np.float64)
+    prev = None
+    for li, lv in enumerate(levels):
+        mesh, C = tuple(lv["mesh"]), int(lv["C"])
+        seeded_feasible = None
+        if li > 0:
+            seeds = seed_from_archive(prev.archive, C, rng)
+            coords = dmr.refine(seeds, prev.mesh)
+        prob = build(mesh, C)
+        groups = synth.single_point_fos(mesh)
+        g = Gomea(prob, coords, groups, mesh, lv["sigma0"], rng)
+        if li > 0:
+            seeded_feasible = float(np.mean(g.obj[:, 3] == 0))
+        curve = g.run(int(lv["generations"]), ref)
+        out.append({"mesh": list(mesh), "C": C, "generations": int(lv["generations"]), "curve": curve,
+                    "final_hv": curve[-1][1] if curve else g.archive.hypervolume(ref),
+                    "archive_size": int(len(g.archive.objs)), "seeded_feasible": seeded_feasible, "gomea": g})
+        prev = g
+    return out

@@ -153,6 +153,48 @@ def sphere_pair(seed=0, n=16, radius=5.0, stretch=1.2, n_guide=5, mesh=3, C=10, 
                 mesh=m, guide=guide, coords=coords, rng=rng)
 
 
+def cube_pair(seed=0, n=50, half=15.0, depth=6.0, r_src=8.0, r_tgt=5.0, v_cube=0.5, v_sphere=1.0, n_guide=20,
+              mesh=6, C=250, amp=0.5):
+    """The paper's synthetic problem (Sec. 2.5): a cube deformed non-affinely
+    with a shrinking sphere at its centre; each side of the cube bends inward
+    as a parabola orthogonal to it; guidance points on the sphere surface.
+    The paper gives no sizes or values; the reading here: an n^3 image, a
+    cube of half-width `half` (value v_cube) on black, a sphere of radius
+    r_src (value v_sphere) at the centre.  In the target every face is pushed
+    towards the centre by depth * (1 - u^2)(1 - w^2) (u, w in-face coordinates
+    scaled to [-1, 1] over the face) and the sphere has radius r_tgt.
+    Guidance: n_guide points on the source sphere and their radial images on
+    the target sphere."""
+    rng = np.random.default_rng(seed)
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    P = [x - c, y - c, z - c]
+
+    def cube(bend):
+        inside = np.ones((n, n, n), bool)
+        for ax in range(3):
+            u, w = P[(ax + 1) % 3] / half, P[(ax + 2) % 3] / half
+            push = bend * np.clip(1.0 - u * u, 0.0, None) * np.clip(1.0 - w * w, 0.0, None)
+            inside &= np.abs(P[ax]) <= half - push
+        return inside
+
+    def image(bend, r):
+        img = np.zeros((n, n, n), np.float32)
+        img[cube(bend)] = v_cube
+        img[P[0] ** 2 + P[1] ** 2 + P[2] ** 2 <= r * r] = v_sphere
+        return img
+
+    src, tgt = image(0.0, r_src), image(depth, r_tgt)
+    d = rng.normal(size=(n_guide, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    guide = np.stack([c + r_src * d, c + r_tgt * d], axis=1)
+    m = (mesh, mesh, mesh)
+    dims = (n, n, n)
+    coords = population(dims, dims, m, C, amp, rng)
+    return dict(name="cube%d" % n, img=(src, tgt), spacing=((1.0, 1.0, 1.0), (1.0, 1.0, 1.0)), mesh=m,
+                guide=guide, coords=coords, rng=rng)
+
+
 def _ellipsoids(n, rng, count=3, values=(0.3, 0.6, 1.0)):
     z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     img = np.zeros((n, n, n), np.float32)
