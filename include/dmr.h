@@ -81,6 +81,11 @@ typedef struct {
   double lambda, mu;     /* Lame parameters of DMR_LINEAR */
   int max_candidates;    /* population capacity, >= 1 */
   void* stream;          /* cudaStream_t to enqueue on; NULL = default stream */
+  const int* guide_set;  /* [n_guide] host: guidance set of each pair, or NULL.
+                            Set form (Sec. 2.3.3): a source point's term is the
+                            smallest squared distance from its mapped position
+                            to the target points of its set, and vice versa;
+                            NULL = every pair its own set (point pairs). */
 } dmr_problem_desc;
 
 /* Create a problem: uploads and converts both images, builds the mirrored

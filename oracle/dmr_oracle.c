@@ -81,6 +81,7 @@ typedef struct {
   int C;
   double* coords; /* [C][2][3][P] */
   dmo_term* terms; /* [C][ntet] */
+  int32_t* gset;   /* [ng] guidance set of each pair (Sec. 2.3.3); NULL: each pair its own set */
   int32_t* loc;    /* [C][2][ng] */
   double* gterm;   /* [C][2][ng] */
   double* sums;    /* [C][4] raw sums */
@@ -510,12 +511,13 @@ static int locate(const dmo_problem* pr, const double* c, int mesh, const double
   return -1;
 }
 
-/* Sec. 2.3.3: squared physical distance between the mapped landmark and its
- * partner.  mesh 0: p_i mapped source->target vs q_i (target spacing);
- * mesh 1: q_i mapped target->source vs p_i (source spacing). */
+/* Sec. 2.3.3: smallest squared physical distance between the mapped guidance
+ * point and the points of its partner set.  mesh 0: p_i mapped
+ * source->target vs the target points q_j of p_i's set (target spacing);
+ * mesh 1: q_i mapped target->source vs the source points p_j (source
+ * spacing).  Each pair its own set: the distance to its partner. */
 static double landmark_term(const dmo_problem* pr, const double* c, int mesh, int i, int t) {
   const double* p = pr->guide + 6 * i + 3 * mesh;
-  const double* q = pr->guide + 6 * i + 3 * (1 - mesh);
   double X[2][4][3];
   tet_vertices(pr, c, mesh, t, X[0]);
   tet_vertices(pr, c, 1 - mesh, t, X[1]);
@@ -523,12 +525,30 @@ static double landmark_term(const dmo_problem* pr, const double* c, int mesh, in
   make_map(X[0], X[1], &M);
   double pm[3];
   apply_map(&M, p, pm);
-  double s = 0;
-  for (int a = 0; a < 3; ++a) {
-    double d = (pm[a] - q[a]) * pr->sp[1 - mesh][a];
-    s += d * d;
+  double best = INFINITY;
+  for (int j = 0; j < pr->ng; ++j) {
+    if (pr->gset ? pr->gset[j] != pr->gset[i] : j != i) continue;
+    const double* q = pr->guide + 6 * j + 3 * (1 - mesh);
+    double s = 0;
+    for (int a = 0; a < 3; ++a) {
+      double d = (pm[a] - q[a]) * pr->sp[1 - mesh][a];
+      s += d * d;
+    }
+    if (s < best) best = s;
   }
-  return s;
+  return best;
+}
+
+/* Guidance sets (Sec. 2.3.3): set_of[i] = set of pair i; NULL restores
+ * one set per pair.  Call before evaluating. */
+void dmo_set_guide_sets(void* h, const int32_t* set_of) {
+  dmo_problem* pr = (dmo_problem*)h;
+  free(pr->gset);
+  pr->gset = NULL;
+  if (set_of && pr->ng > 0) {
+    pr->gset = (int32_t*)malloc(sizeof(int32_t) * pr->ng);
+    memcpy(pr->gset, set_of, sizeof(int32_t) * pr->ng);
+  }
 }
 
 /* ------------------------------------------------------------ problem */
@@ -583,6 +603,7 @@ void dmo_destroy(void* h) {
   free(pr->fixmask);
   free(pr->rest_vol);
   free(pr->guide);
+  free(pr->gset);
   free(pr);
 }
 

@@ -58,6 +58,7 @@ def _load():
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_double]
         lib.dmo_destroy.argtypes = [vp]
+        lib.dmo_set_guide_sets.argtypes = [vp, ctypes.c_void_p]
         lib.dmo_ntet.argtypes = [vp]
         lib.dmo_npoints.argtypes = [vp]
         lib.dmo_get_tets.argtypes = [vp, _i32p]
@@ -121,7 +122,7 @@ class Oracle:
     population state used for partial evaluation."""
 
     def __init__(self, img_s, img_t, spacing_s, spacing_t, mesh_pts, guide=None,
-                 black_rule=True, model=SPRING, lam=1.0, mu=1.0):
+                 black_rule=True, model=SPRING, lam=1.0, mu=1.0, guide_sets=None):
         self._lib = _load()
         img_s = _f64(img_s)
         img_t = _f64(img_t)
@@ -137,6 +138,11 @@ class Oracle:
                                       self.ng, int(bool(black_rule)), self.model,
                                       float(lam), float(mu))
         self.ntet = self._lib.dmo_ntet(self.h)
+        self._gsets = None
+        if guide_sets is not None and self.ng:
+            self._gsets = _i32(guide_sets)
+            assert self._gsets.shape == (self.ng,)
+            self._lib.dmo_set_guide_sets(self.h, self._gsets.ctypes.data)
         self.P = self._lib.dmo_npoints(self.h)
         self.C = 0
         self._last_ntr = 0

@@ -161,6 +161,10 @@ struct dmr_problem {
   uint8_t* d_fix = nullptr;
   float* d_restvol = nullptr;
   double* d_guide = nullptr;
+  std::vector<int> gs_id, gs_ptr, gs_mem;  // guidance sets (empty: one set per pair)
+  int* d_gs_id = nullptr;
+  int* d_gs_ptr = nullptr;
+  int* d_gs_mem = nullptr;
   double* d_coords = nullptr;
   double* d_ssd = nullptr;
   int* d_cov = nullptr;
@@ -297,6 +301,7 @@ void release_problem(dmr_problem* p) {
     dfree(p->cmask[k]);
   }
   dfree(p->d_tet); dfree(p->d_fperm); dfree(p->d_fix); dfree(p->d_restvol); dfree(p->d_guide);
+  dfree(p->d_gs_id); dfree(p->d_gs_ptr); dfree(p->d_gs_mem);
   dfree(p->d_coords); dfree(p->d_ssd); dfree(p->d_cov); dfree(p->d_def); dfree(p->d_fold);
   dfree(p->d_loc); dfree(p->d_gterm); dfree(p->d_sums); dfree(p->d_samples); dfree(p->d_prob); dfree(p->d_obj);
   dfree(p->d_gptr); dfree(p->d_gpts);
@@ -383,6 +388,22 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       delete p;
       return fail(DMR_EINVAL, "non-finite guidance coordinate");
     }
+  if (d->guide_set && p->ng > 0) {
+    // compact set ids in order of first appearance; members in pair order
+    std::vector<int> ids(d->guide_set, d->guide_set + p->ng), uniq;
+    p->gs_id.resize(p->ng);
+    for (int i = 0; i < p->ng; ++i) {
+      auto it = std::find(uniq.begin(), uniq.end(), ids[i]);
+      p->gs_id[i] = (int)(it - uniq.begin());
+      if (it == uniq.end()) uniq.push_back(ids[i]);
+    }
+    p->gs_ptr.assign(uniq.size() + 1, 0);
+    for (int i = 0; i < p->ng; ++i) ++p->gs_ptr[p->gs_id[i] + 1];
+    for (size_t k = 0; k < uniq.size(); ++k) p->gs_ptr[k + 1] += p->gs_ptr[k];
+    p->gs_mem.resize(p->ng);
+    std::vector<int> fill(p->gs_ptr.begin(), p->gs_ptr.end() - 1);
+    for (int i = 0; i < p->ng; ++i) p->gs_mem[fill[p->gs_id[i]]++] = i;
+  }
   build_topology(p);
   // images: input -> storage, plain + corner-packed cells
   for (int k = 0; k < 2; ++k) {
@@ -456,6 +477,14 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
         (rc = dalloc(&p->d_gterm, C * 2 * std::max(1, p->ng))) || (rc = dalloc(&p->d_sums, C * 4)) ||
         (rc = dalloc(&p->d_samples, 1)) || (rc = dalloc(&p->d_prob, 1)) || (rc = dalloc(&p->d_obj, C * 4)))
       goto fail_;
+    if (!p->gs_id.empty()) {
+      if ((rc = dalloc(&p->d_gs_id, p->gs_id.size())) || (rc = dalloc(&p->d_gs_ptr, p->gs_ptr.size())) ||
+          (rc = dalloc(&p->d_gs_mem, p->gs_mem.size())))
+        goto fail_;
+      cudaMemcpyAsync(p->d_gs_id, p->gs_id.data(), sizeof(int) * p->gs_id.size(), cudaMemcpyHostToDevice, p->st);
+      cudaMemcpyAsync(p->d_gs_ptr, p->gs_ptr.data(), sizeof(int) * p->gs_ptr.size(), cudaMemcpyHostToDevice, p->st);
+      cudaMemcpyAsync(p->d_gs_mem, p->gs_mem.data(), sizeof(int) * p->gs_mem.size(), cudaMemcpyHostToDevice, p->st);
+    }
     cudaMemcpyAsync(p->d_tet, t4.data(), sizeof(int4) * p->ntet, cudaMemcpyHostToDevice, p->st);
     cudaMemcpyAsync(p->d_fperm, p->fperm.data(), sizeof(uint32_t) * p->ntet, cudaMemcpyHostToDevice, p->st);
     cudaMemcpyAsync(p->d_fix, p->fixmask.data(), p->P, cudaMemcpyHostToDevice, p->st);
@@ -493,6 +522,9 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
     h.guid_norm = 2.0 * std::max(1, p->ng);
     h.ng = p->ng;
     h.guide = p->d_guide;
+    h.gsid = p->d_gs_id;
+    h.gptr = p->d_gs_ptr;
+    h.gmem = p->d_gs_mem;
     h.C = 0;
     h.coords = p->d_coords;
     h.c_ssd = p->d_ssd;

@@ -43,6 +43,11 @@ struct DevProblem {
   double sim_norm, def_norm, guid_norm;
   int ng;
   const double* guide;      // [ng][2][3]
+  // guidance sets (NULL: each pair its own set): set index of each pair,
+  // set s holds the pairs gmem[gptr[s] .. gptr[s+1])
+  const int* gsid;
+  const int* gptr;
+  const int* gmem;
   // population state
   int C;
   double* coords;           // [C][2][3][P]

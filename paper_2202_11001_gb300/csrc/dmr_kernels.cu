@@ -551,19 +551,41 @@ __device__ __forceinline__ bool vol_positive(const ItemRec& r) {
   return v > 0 && isfinite(v);
 }
 
-__device__ double landmark_term(const ItemRec& r, const DevProblem& pr, const double p[3], const double q[3]) {
+// Squared physical distance of a mapped guidance point pm (in the partner
+// image of mesh `mesh`) from partner point q, in the partner's spacing.
+__device__ __forceinline__ double landmark_dist2(const DevProblem& pr, const double pm[3], const double* q, int mesh) {
+  const int dp = 1 - mesh;
+  double s = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double d = dmul(dsub(pm[a], q[a]), pr.spd[dp][a]);
+    s = dadd(s, dmul(d, d));
+  }
+  return s;
+}
+
+// Sec. 2.3.3: smallest squared physical distance between guidance point i
+// of mesh `mesh` (at p), mapped through the record's tet, and the partner
+// points of its set (its own partner when there are no sets).
+__device__ double landmark_term(const ItemRec& r, const DevProblem& pr, const double p[3], int mesh, int i) {
   // mapped landmark (v + d0) + G (v - own_0) with the record's FP64 map
   double pm[3];
   for (int c = 0; c < 3; ++c)
     pm[c] = (p[c] + (r.XP[0][c] - r.X[0][c])) +
             fma(r.Gd[c][0], p[0] - r.X[0][0], fma(r.Gd[c][1], p[1] - r.X[0][1], r.Gd[c][2] * (p[2] - r.X[0][2])));
-  int dp = 1 - r.dir;
-  double s = 0.0;
-  for (int a = 0; a < 3; ++a) {
-    double d = dmul(dsub(pm[a], q[a]), pr.spd[dp][a]);
-    s = dadd(s, dmul(d, d));
+  int k0 = 0, k1 = 1;
+  if (pr.gsid) {
+    const int s = pr.gsid[i];
+    k0 = pr.gptr[s];
+    k1 = pr.gptr[s + 1];
   }
-  return s;
+  double best = INFINITY;
+  for (int k = k0; k < k1; ++k) {
+    const int j = pr.gsid ? pr.gmem[k] : i;
+    const double* q = pr.guide + 6 * j + 3 * (1 - mesh);
+    const double t = landmark_dist2(pr, pm, q, mesh);
+    best = t < best ? t : best;
+  }
+  return best;
 }
 
 // Test one tet record for landmark p: volume sign first (folded tets never
@@ -586,11 +608,8 @@ __global__ void k_locate_full(const DevProblem* probs, Batch b, int c0, int nc) 
   int rem = gw % (2 * ng);
   int mesh = rem / ng, i = rem % ng;
   int cand = c0 + ci;
-  double p[3], q[3];
-  for (int a = 0; a < 3; ++a) {
-    p[a] = pr.guide[6 * i + 3 * mesh + a];
-    q[a] = pr.guide[6 * i + 3 * (1 - mesh) + a];
-  }
+  double p[3];
+  for (int a = 0; a < 3; ++a) p[a] = pr.guide[6 * i + 3 * mesh + a];
   float pmag = fmaxf(fabsf((float)p[0]), fmaxf(fabsf((float)p[1]), fabsf((float)p[2])));
   int found = -1;
   for (int tb = 0; tb < pr.ntet && found < 0; tb += 32) {
@@ -606,7 +625,7 @@ __global__ void k_locate_full(const DevProblem* probs, Batch b, int c0, int nc) 
   if (lane == 0) {
     size_t li = ((size_t)cand * 2 + mesh) * ng + i;
     pr.c_loc[li] = found;
-    pr.c_gterm[li] = found >= 0 ? landmark_term(b.rec[2 * ((size_t)ci * pr.ntet + found) + mesh], pr, p, q) : 0.0;
+    pr.c_gterm[li] = found >= 0 ? landmark_term(b.rec[2 * ((size_t)ci * pr.ntet + found) + mesh], pr, p, mesh, i) : 0.0;
   }
 }
 
@@ -707,11 +726,8 @@ __global__ void __launch_bounds__(32 * kLmWarps, 3) k_landmarks_partial(const De
       int ee = base + src;
       int mesh = ee / ng, i = ee % ng;
       int t_old = __shfl_sync(FULL_MASK, told, src);
-      double p[3], q[3];
-      for (int a = 0; a < 3; ++a) {
-        p[a] = pr.guide[6 * i + 3 * mesh + a];
-        q[a] = pr.guide[6 * i + 3 * (1 - mesh) + a];
-      }
+      double p[3];
+      for (int a = 0; a < 3; ++a) p[a] = pr.guide[6 * i + 3 * mesh + a];
       float pmag = fmaxf(fabsf((float)p[0]), fmaxf(fabsf((float)p[1]), fabsf((float)p[2])));
       int found = -1;
       for (int jb = 0; jb < ntt && found < 0; jb += 32) {
@@ -725,7 +741,7 @@ __global__ void __launch_bounds__(32 * kLmWarps, 3) k_landmarks_partial(const De
         if (m) found = jb + __ffs(m) - 1;
       }
       if (lane == 0) {
-        double term = found >= 0 ? landmark_term(b.rec[2 * (size_t)(first + found) + mesh], pr, p, q) : 0.0;
+        double term = found >= 0 ? landmark_term(b.rec[2 * (size_t)(first + found) + mesh], pr, p, mesh, i) : 0.0;
         size_t li = ((size_t)cand * 2 + mesh) * ng + i;
         double old = pr.c_gterm[li];
         gd = dadd(gd, dsub(term, old));

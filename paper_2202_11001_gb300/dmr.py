@@ -42,6 +42,7 @@ class _Desc(ctypes.Structure):
         ("mu", ctypes.c_double),
         ("max_candidates", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("guide_set", ctypes.c_void_p),
     ]
 
 
@@ -219,7 +220,7 @@ class Problem:
 
     def __init__(self, img_s, img_t, spacing_s, spacing_t, mesh_pts, guide=None, black_rule=True,
                  model=SPRING, lam=1.0, mu=1.0, storage="f32", max_candidates=1, stream=None,
-                 img_dtype=None):
+                 img_dtype=None, guide_sets=None):
         lib = load()
         self._lib = lib
         d = _Desc()
@@ -254,6 +255,12 @@ class Problem:
             d.guide = g.ctypes.data
             d.n_guide = g.shape[0]
             self.ng = g.shape[0]
+            if guide_sets is not None:
+                gs = np.ascontiguousarray(np.asarray(guide_sets, np.int32).reshape(-1))
+                if gs.shape[0] != self.ng:
+                    raise ValueError("guide_sets needs one set id per guidance pair")
+                self._gsets = gs
+                d.guide_set = gs.ctypes.data
         d.black_rule = int(bool(black_rule))
         d.deform_model = int(model)
         d.lam = float(lam)
