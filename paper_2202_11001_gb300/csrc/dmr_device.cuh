@@ -121,34 +121,6 @@ static __device__ __forceinline__ float load_plain_dyn(const void* p, int st, lo
   return load_plain<ST_F16>(p, i);
 }
 
-// Trilinear interpolation of a corner-packed cell: corner index dx+2dy+4dz.
-template <int ST>
-static __device__ __forceinline__ float cell_lerp(const void* cells, unsigned idx, float fx, float fy, float fz) {
-  float c0, c1, c2, c3, c4, c5, c6, c7;
-  if (ST == ST_F32) {
-    const float4* p = (const float4*)cells + 2 * (size_t)idx;
-    float4 a = __ldg(p), b = __ldg(p + 1);
-    c0 = a.x; c1 = a.y; c2 = a.z; c3 = a.w; c4 = b.x; c5 = b.y; c6 = b.z; c7 = b.w;
-  } else {
-    uint4 w = __ldg((const uint4*)cells + idx);
-    if (ST == ST_BF16) {
-      c0 = bf16lo(w.x); c1 = bf16hi(w.x); c2 = bf16lo(w.y); c3 = bf16hi(w.y);
-      c4 = bf16lo(w.z); c5 = bf16hi(w.z); c6 = bf16lo(w.w); c7 = bf16hi(w.w);
-    } else {
-      c0 = f16lo(w.x); c1 = f16hi(w.x); c2 = f16lo(w.y); c3 = f16hi(w.y);
-      c4 = f16lo(w.z); c5 = f16hi(w.z); c6 = f16lo(w.w); c7 = f16hi(w.w);
-    }
-  }
-  float a0 = fmaf(fx, c1 - c0, c0);
-  float a1 = fmaf(fx, c3 - c2, c2);
-  float a2 = fmaf(fx, c5 - c4, c4);
-  float a3 = fmaf(fx, c7 - c6, c6);
-  float b0 = fmaf(fy, a1 - a0, a0);
-  float b1 = fmaf(fy, a3 - a2, a2);
-  return fmaf(fz, b1 - b0, b0);
-}
-
-
 static __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -379,7 +351,15 @@ template <int ST>
 static __device__ __forceinline__ float cell_interp(const Cell<ST>& c, float fx, float fy, float fz) {
   float c0, c1, c2, c3, c4, c5, c6, c7;
   if constexpr (ST == ST_F32) {
-    c0 = c.a.x; c1 = c.a.y; c2 = c.a.z; c3 = c.a.w; c4 = c.b.x; c5 = c.b.y; c6 = c.b.z; c7 = c.b.w;
+    // f32 cells hold (c0, c1 - c0, c2, c3 - c2, c4, c5 - c4, c6, c7 - c6): the
+    // same FP32 differences the first level would form, one FMA each
+    const float a0 = fmaf(fx, c.a.y, c.a.x);
+    const float a1 = fmaf(fx, c.a.w, c.a.z);
+    const float a2 = fmaf(fx, c.b.y, c.b.x);
+    const float a3 = fmaf(fx, c.b.w, c.b.z);
+    const float b0 = fmaf(fy, a1 - a0, a0);
+    const float b1 = fmaf(fy, a3 - a2, a2);
+    return fmaf(fz, b1 - b0, b0);
   } else if constexpr (ST == ST_BF16) {
     c0 = bf16lo(c.w.x); c1 = bf16hi(c.w.x); c2 = bf16lo(c.w.y); c3 = bf16hi(c.w.y);
     c4 = bf16lo(c.w.z); c5 = bf16hi(c.w.z); c6 = bf16lo(c.w.w); c7 = bf16hi(c.w.w);

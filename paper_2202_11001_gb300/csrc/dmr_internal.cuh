@@ -19,8 +19,9 @@ enum { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
 struct DevProblem {
   // images: plain [nz][ny][nx] and corner-packed cells
   // [(nz+2)][(ny+2)][(nx+2)] x 8 corners for cell origins -1..n per axis
-  // (corner values pre-clamped to the image), plus per-cell zero flags
-  // (bit0: some corner is 0, bit1: all corners are 0).
+  // (corner values pre-clamped to the image; f32 cells store each x pair as
+  // value and difference), plus per-cell zero flags (bit0: some corner is 0,
+  // bit1: all corners are 0, bits 2/3: the 4x4x4 block all / none 0).
   const void* plain[2];
   const void* cells[2];
   const uint8_t* cflag[2];

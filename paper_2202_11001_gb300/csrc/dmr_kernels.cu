@@ -83,9 +83,11 @@ __global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz,
       }
   cmask[id] = zm;
   if (st == ST_F32) {
+    // corner pairs along x as (value, difference): the interpolation's first
+    // level then needs one FMA per pair (the same FP32 difference)
     float4* p = (float4*)cells + 2 * id;
-    p[0] = make_float4(fv[0], fv[1], fv[2], fv[3]);
-    p[1] = make_float4(fv[4], fv[5], fv[6], fv[7]);
+    p[0] = make_float4(fv[0], fv[1] - fv[0], fv[2], fv[3] - fv[2]);
+    p[1] = make_float4(fv[4], fv[5] - fv[4], fv[6], fv[7] - fv[6]);
   } else {
     uint4 w;
     w.x = raw[0] | (raw[1] << 16);
@@ -112,16 +114,6 @@ __device__ __forceinline__ double vcoord(const DevProblem& pr, const Batch& b, i
 }
 
 __device__ __forceinline__ float fabs3max(float a, float b, float c) { return fmaxf(fabsf(a), fmaxf(fabsf(b), fabsf(c))); }
-
-// Edge vector X_j - X_i (i != j, local ids), negated if flip, from the six
-// edges E6 = {01, 02, 03, 12, 13, 23} (x - y = -(y - x) exactly), without
-// indexing local memory.
-__device__ __forceinline__ double edge6(const double (&E)[6][3], int i, int j, int a, bool flip) {
-  const int lo = min(i, j), hi = max(i, j);
-  const int k = lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5);
-  const double v = k == 0 ? E[0][a] : k == 1 ? E[1][a] : k == 2 ? E[2][a] : k == 3 ? E[3][a] : k == 4 ? E[4][a] : E[5][a];
-  return (i < j) != flip ? v : -v;
-}
 
 // v[i][a] for a runtime vertex index i without indexing local memory
 __device__ __forceinline__ double pick4d(const double (&v)[4][3], int i, int a) {
@@ -351,20 +343,19 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
       }
       R.vr[i][3] = 0.f;
     }
-    // faces: FP64 normals from the six edge vectors (fused cross products,
-    // within 2^-51 U W of the oracle's) and FP64 offsets B = -s n.(a - O),
+    // faces: inward FP64 normals from the adjugate rows of the map (for a
+    // tet of positive volume, rr[m-1] is the inward normal, with the length
+    // of a face cross product, of the face opposite vertex m = 1, 2, 3, and
+    // -(rr[0] + rr[1] + rr[2]) that of the face opposite vertex 0; within a
+    // few 2^-53 U W of the oracle's normals) and FP64 offsets B = -n.(a - O),
     // each rounded once to FP32.  At a voxel q = p - O of the box
     // (0 <= q < L), h(q) = fl(A.q + B) differs from the FP64 predicate by at
     // most eps (an L + |B|) from rounding A and B, plus 3 eps (an L + |B|)
     // from the evaluation (eps = 2^-24), plus 1.5e-14 (U W + an)(L + V) for
     // the FP64 predicate's own rounding.  The margin takes twice the FP32
     // part: 2^-21 (an L + |B|).
-    const double E6[6][3] = {{eo[0][0], eo[0][1], eo[0][2]},
-                             {eo[1][0], eo[1][1], eo[1][2]},
-                             {eo[2][0], eo[2][1], eo[2][2]},
-                             {dsub(own[2][0], own[1][0]), dsub(own[2][1], own[1][1]), dsub(own[2][2], own[1][2])},
-                             {dsub(own[3][0], own[1][0]), dsub(own[3][1], own[1][1]), dsub(own[3][2], own[1][2])},
-                             {dsub(own[3][0], own[2][0]), dsub(own[3][1], own[2][1]), dsub(own[3][2], own[2][2])}};
+    const double N0[3] = {-((rr[0][0] + rr[1][0]) + rr[2][0]), -((rr[0][1] + rr[1][1]) + rr[2][1]),
+                          -((rr[0][2] + rr[1][2]) + rr[2][2])};
     const uint32_t fp = pr.fperm[t];
     const float Lf = (float)L;
     // edge magnitudes are bounded by the box extent: |u|, |w| <= ext
@@ -372,16 +363,10 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
     const float UW = ext * ext;
     for (int f = 0; f < 4; ++f) {
       const int ia = face_local(fp, f, 0), ib = face_local(fp, f, 1), ic = face_local(fp, f, 2);
-      // inward sign folded into the first edge: s (u x w) = (s u) x w
-      const bool flip = face_sign(fp, f) < 0;
-      double u[3], w[3];
-      for (int a = 0; a < 3; ++a) {
-        u[a] = edge6(E6, ia, ib, a, flip);
-        w[a] = edge6(E6, ia, ic, a, false);
-      }
-      const double nx = fma(u[1], w[2], -u[2] * w[1]);
-      const double ny = fma(u[2], w[0], -u[0] * w[2]);
-      const double nz = fma(u[0], w[1], -u[1] * w[0]);
+      const int opp = 6 - ia - ib - ic;  // the vertex not on face f
+      const double nx = opp == 0 ? N0[0] : opp == 1 ? rr[0][0] : opp == 2 ? rr[1][0] : rr[2][0];
+      const double ny = opp == 0 ? N0[1] : opp == 1 ? rr[0][1] : opp == 2 ? rr[1][1] : rr[2][1];
+      const double nz = opp == 0 ? N0[2] : opp == 1 ? rr[0][2] : opp == 2 ? rr[1][2] : rr[2][2];
       const double Bd = -fma(nx, pick4d(vd, ia, 0), fma(ny, pick4d(vd, ia, 1), nz * pick4d(vd, ia, 2)));
       const float Ax = (float)nx, Ay = (float)ny, Az = (float)nz, Bp = (float)Bd;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
