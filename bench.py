@@ -619,7 +619,7 @@ def main():
             pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
             per_wave.append((pin(gids), pin(cids), pin(tc), torch.empty((len(gids), 4), dtype=torch.float64,
                                                                         pin_memory=True)))
-            h2d += gids.nbytes + cids.nbytes + tc.nbytes
+            h2d += tc.nbytes  # group / candidate ids repeat: the library keeps their layout on the device
             d2h += len(gids) * 4 * 8 + len(gids)
         g.samples(reset=True)
         torch.cuda.synchronize()
@@ -632,7 +632,8 @@ def main():
         dt = time.perf_counter() - t0
         e2e = {"value": g.samples(reset=True) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "path": "dmr_eval_partial + dmr_commit_improving per wave, pinned "
-                                                       "host buffers"}
+                                                       "host buffers; trial layouts cached by the library after the "
+                                                       "first generation"}
 
     peaks, peak_kind = measured_peaks()
     clock_max = clocks.get("sm_max_mhz") or 2070.0

@@ -126,7 +126,11 @@ int dmr_eval_full(dmr_problem* p, int n_cand, const double* coords, double* obj_
  *   new = stored - sum_{touched} old + sum_{touched} new.
  * group_ids, cand_ids: [n_trials] (host or device); trial_coords:
  * [n_trials][2][3][G] FP64 (host or device); obj_out [n_trials][4].
- * The committed state is unchanged; dmr_commit applies accepted trials. */
+ * The committed state is unchanged; dmr_commit applies accepted trials.
+ * The library keeps the derived trial lists of the 16 most recent
+ * (group_ids, cand_ids) layouts on the device, so repeating a layout (as an
+ * optimiser does every generation) uploads only trial_coords.  With obj_out
+ * in device memory the call returns without waiting for the device. */
 int dmr_eval_partial(dmr_problem* p, int n_trials, const int* group_ids, const int* cand_ids,
                      const double* trial_coords, double* obj_out);
 

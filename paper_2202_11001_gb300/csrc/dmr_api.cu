@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cstring>
+
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -131,6 +133,28 @@ struct Scratch {
 
 }  // namespace
 
+namespace {
+// A trial layout of dmr_eval_partial (the group and candidate of every
+// trial) with its derived lists, on the host and on the device.  Optimisers
+// repeat the same layouts every generation (one per wave), so the library
+// keeps the most recent ones and a repeated call uploads only the trial
+// coordinates.
+struct Layout {
+  std::vector<int> gid, cid, first, ntt, cptr, ctr;
+  int tot = 0, max_cid = 0;
+  bool safe = true;
+  unsigned long long used = 0;
+  int *tt_trial = nullptr, *tt_tet = nullptr, *tr_cand = nullptr, *tr_group = nullptr, *tr_first = nullptr,
+      *tr_ntt = nullptr, *cand_ptr = nullptr, *cand_trials = nullptr;
+  uint32_t* tt_slot = nullptr;
+  void release() {
+    dfree(tt_trial); dfree(tt_tet); dfree(tt_slot); dfree(tr_cand); dfree(tr_group); dfree(tr_first); dfree(tr_ntt);
+    dfree(cand_ptr); dfree(cand_trials);
+  }
+};
+constexpr int kLayoutCache = 16;
+}  // namespace
+
 struct dmr_problem {
   int dev = 0;
   cudaStream_t st = nullptr;
@@ -186,6 +210,9 @@ struct dmr_problem {
   // scratch and last partial evaluation
   Scratch sc;
   bool have_partial = false, partial_safe = false;
+  std::vector<Layout*> layouts;  // recent eval_partial layouts
+  unsigned long long layout_clock = 0;
+  Layout* cur = nullptr;         // layout of the last eval_partial
   int last_ntr = 0, last_ntt = 0;
   std::vector<int> last_cand, last_group, last_first, last_ntt_v;
   int last_nlist = 0;
@@ -293,7 +320,17 @@ void build_topology(dmr_problem* p) {
       }
 }
 
+void clear_layouts(dmr_problem* p) {
+  for (Layout* L : p->layouts) {
+    L->release();
+    delete L;
+  }
+  p->layouts.clear();
+  p->cur = nullptr;
+}
+
 void release_problem(dmr_problem* p) {
+  clear_layouts(p);
   for (int k = 0; k < 2; ++k) {
     dfree(p->plain[k]);
     dfree(p->cells[k]);
@@ -688,6 +725,7 @@ int dmr_set_fos(dmr_problem* p, int n_groups, const int* group_ptr, const int* g
   CU(cudaMemcpyAsync(p->d_gpts, pts.data(), sizeof(int) * pts.size(), cudaMemcpyHostToDevice, p->st));
   CU(cudaStreamSynchronize(p->st));
   p->have_partial = false;
+  clear_layouts(p);  // group ids now mean other groups
   return DMR_OK;
 }
 
@@ -739,6 +777,19 @@ Batch make_batch(dmr_problem* p, Scratch& s, int n_tt, int n_tr) {
   b.aff_term = s.aff_term;
   b.tr_delta = s.tr_delta;
   b.tr_obj = s.tr_obj;
+  return b;
+}
+
+// The batch of a cached eval_partial layout: lists from the layout, outputs
+// and records in the problem's scratch.
+Batch layout_batch(dmr_problem* p, Layout* L, int n_tr) {
+  Batch b = make_batch(p, p->sc, L->tot, n_tr);
+  b.tt_trial = L->tt_trial;
+  b.tt_tet = L->tt_tet;
+  b.tt_slot = L->tt_slot;
+  b.tr_cand = L->tr_cand;
+  b.tr_first = L->tr_first;
+  b.tr_ntt = L->tr_ntt;
   return b;
 }
 
@@ -805,68 +856,113 @@ int dmr_eval_partial(dmr_problem* p, int n_trials, const int* group_ids, const i
   if (p->C == 0) return fail(DMR_ESTATE, "no population (call dmr_eval_full first)");
   if (n_trials < 1) return fail(DMR_EINVAL, "n_trials must be >= 1");
   std::vector<int> gid(n_trials), cid(n_trials);
-  CU(cudaMemcpy(gid.data(), group_ids, sizeof(int) * n_trials, cudaMemcpyDefault));
-  CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n_trials, cudaMemcpyDefault));
-  std::vector<int> first(n_trials), ntt(n_trials);
-  long tot = 0;
-  for (int k = 0; k < n_trials; ++k) {
-    if (gid[k] < 0 || gid[k] >= p->n_groups) return fail(DMR_EINVAL, "group id out of range");
-    if (cid[k] < 0 || cid[k] >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
-    first[k] = (int)tot;
-    ntt[k] = p->g_tptr[gid[k] + 1] - p->g_tptr[gid[k]];
-    tot += ntt[k];
-  }
-  if (tot > (1L << 30)) return fail(DMR_EINVAL, "too many trial tets");
-  int rc;
-  if ((rc = p->sc.ensure((int)tot, n_trials, p->gmax, 2 * std::max(1, p->ng)))) return rc;
-  std::vector<int> tt_trial(tot), tt_tet(tot);
-  std::vector<uint32_t> tt_slot(tot);
-  for (int k = 0; k < n_trials; ++k) {
-    int g = gid[k];
-    for (int j = 0; j < ntt[k]; ++j) {
-      tt_trial[first[k] + j] = k;
-      tt_tet[first[k] + j] = p->g_tets[p->g_tptr[g] + j];
-      tt_slot[first[k] + j] = p->g_slot[p->g_tptr[g] + j];
-    }
-  }
-  // commit safety: accepted trials of a candidate must touch disjoint tets
-  std::vector<int> order(n_trials);
-  for (int k = 0; k < n_trials; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cid[a] < cid[b]; });
-  std::vector<int> cptr(1, 0), ctr;
-  bool safe = true;
-  {
-    std::vector<int> stamp(p->ntet, -1);
-    int prev = -1, ci = -1;
-    for (int idx : order) {
-      if (cid[idx] != prev) {
-        prev = cid[idx];
-        ++ci;
-        if (ci > 0) cptr.push_back((int)ctr.size());
-      }
-      ctr.push_back(idx);
-      int g = gid[idx];
-      for (int j = p->g_tptr[g]; j < p->g_tptr[g + 1]; ++j) {
-        int t = p->g_tets[j];
-        if (stamp[t] == cid[idx]) safe = false;
-        stamp[t] = cid[idx];
-      }
-    }
-    cptr.push_back((int)ctr.size());
-  }
+  if (is_device_ptr(group_ids)) CU(cudaMemcpy(gid.data(), group_ids, sizeof(int) * n_trials, cudaMemcpyDeviceToHost));
+  else std::memcpy(gid.data(), group_ids, sizeof(int) * n_trials);
+  if (is_device_ptr(cand_ids)) CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n_trials, cudaMemcpyDeviceToHost));
+  else std::memcpy(cid.data(), cand_ids, sizeof(int) * n_trials);
   const cudaStream_t st = p->st;
-  CU(cudaMemcpyAsync(p->sc.tt_trial, tt_trial.data(), sizeof(int) * tot, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.tt_tet, tt_tet.data(), sizeof(int) * tot, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.tt_slot, tt_slot.data(), sizeof(uint32_t) * tot, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.tr_cand, cid.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.tr_group, gid.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.tr_first, first.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.tr_ntt, ntt.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.cand_ptr, cptr.data(), sizeof(int) * cptr.size(), cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(p->sc.cand_trials, ctr.data(), sizeof(int) * ctr.size(), cudaMemcpyHostToDevice, st));
+  int rc;
+  Layout* L = nullptr;
+  for (Layout* c : p->layouts)
+    if (c->gid == gid && c->cid == cid) {
+      if (c->max_cid >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+      L = c;
+      break;
+    }
+  if (!L) {
+    std::vector<int> first(n_trials), ntt(n_trials);
+    long tot = 0;
+    for (int k = 0; k < n_trials; ++k) {
+      if (gid[k] < 0 || gid[k] >= p->n_groups) return fail(DMR_EINVAL, "group id out of range");
+      if (cid[k] < 0 || cid[k] >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+      first[k] = (int)tot;
+      ntt[k] = p->g_tptr[gid[k] + 1] - p->g_tptr[gid[k]];
+      tot += ntt[k];
+    }
+    if (tot > (1L << 30)) return fail(DMR_EINVAL, "too many trial tets");
+    std::vector<int> tt_trial(tot), tt_tet(tot);
+    std::vector<uint32_t> tt_slot(tot);
+    for (int k = 0; k < n_trials; ++k) {
+      int g = gid[k];
+      for (int j = 0; j < ntt[k]; ++j) {
+        tt_trial[first[k] + j] = k;
+        tt_tet[first[k] + j] = p->g_tets[p->g_tptr[g] + j];
+        tt_slot[first[k] + j] = p->g_slot[p->g_tptr[g] + j];
+      }
+    }
+    // commit safety: accepted trials of a candidate must touch disjoint tets
+    std::vector<int> order(n_trials);
+    for (int k = 0; k < n_trials; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cid[a] < cid[b]; });
+    std::vector<int> cptr(1, 0), ctr;
+    bool safe = true;
+    {
+      std::vector<int> stamp(p->ntet, -1);
+      int prev = -1, ci = -1;
+      for (int idx : order) {
+        if (cid[idx] != prev) {
+          prev = cid[idx];
+          ++ci;
+          if (ci > 0) cptr.push_back((int)ctr.size());
+        }
+        ctr.push_back(idx);
+        int g = gid[idx];
+        for (int j = p->g_tptr[g]; j < p->g_tptr[g + 1]; ++j) {
+          int t = p->g_tets[j];
+          if (stamp[t] == cid[idx]) safe = false;
+          stamp[t] = cid[idx];
+        }
+      }
+      cptr.push_back((int)ctr.size());
+    }
+    if ((int)p->layouts.size() >= kLayoutCache) {
+      // evict the least recently used layout (cudaFree waits for its users)
+      auto it = std::min_element(p->layouts.begin(), p->layouts.end(),
+                                 [](const Layout* x, const Layout* y) { return x->used < y->used; });
+      (*it)->release();
+      delete *it;
+      p->layouts.erase(it);
+    }
+    L = new Layout();
+    L->gid = gid;
+    L->cid = cid;
+    L->first = std::move(first);
+    L->ntt = std::move(ntt);
+    L->cptr = std::move(cptr);
+    L->ctr = std::move(ctr);
+    L->tot = (int)tot;
+    L->safe = safe;
+    L->max_cid = *std::max_element(cid.begin(), cid.end());
+    if ((rc = dalloc(&L->tt_trial, (size_t)std::max(1L, tot))) || (rc = dalloc(&L->tt_tet, (size_t)std::max(1L, tot))) ||
+        (rc = dalloc(&L->tt_slot, (size_t)std::max(1L, tot))) || (rc = dalloc(&L->tr_cand, n_trials)) ||
+        (rc = dalloc(&L->tr_group, n_trials)) || (rc = dalloc(&L->tr_first, n_trials)) ||
+        (rc = dalloc(&L->tr_ntt, n_trials)) || (rc = dalloc(&L->cand_ptr, L->cptr.size())) ||
+        (rc = dalloc(&L->cand_trials, std::max<size_t>(1, L->ctr.size())))) {
+      L->release();
+      delete L;
+      return rc;
+    }
+    // the host vectors live as long as the layout, so the copies may stay in flight
+    CU(cudaMemcpyAsync(L->tt_trial, tt_trial.data(), sizeof(int) * tot, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->tt_tet, tt_tet.data(), sizeof(int) * tot, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->tt_slot, tt_slot.data(), sizeof(uint32_t) * tot, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->tr_cand, L->cid.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->tr_group, L->gid.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->tr_first, L->first.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->tr_ntt, L->ntt.data(), sizeof(int) * n_trials, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->cand_ptr, L->cptr.data(), sizeof(int) * L->cptr.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(L->cand_trials, L->ctr.data(), sizeof(int) * L->ctr.size(), cudaMemcpyHostToDevice, st));
+    // tt_* are pageable temporaries: their copies are staged before the calls return
+    p->layouts.push_back(L);
+  }
+  L->used = ++p->layout_clock;
+  p->cur = L;
+  const long tot = L->tot;
+  const bool safe = L->safe;
+  if ((rc = p->sc.ensure((int)tot, n_trials, p->gmax, 2 * std::max(1, p->ng)))) return rc;
   CU(cudaMemcpyAsync(p->sc.tr_coords, trial_coords, sizeof(double) * 6 * p->gmax * (size_t)n_trials, cudaMemcpyDefault,
                      st));
-  Batch b = make_batch(p, p->sc, (int)tot, n_trials);
+  Batch b = layout_batch(p, L, n_trials);
   launch_setup(p->d_prob, b, st);
   if (p->ng > 0 && !p->st2) {
     CU(cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking));
@@ -886,26 +982,25 @@ int dmr_eval_partial(dmr_problem* p, int n_trials, const int* group_ids, const i
   CU(cudaGetLastError());
   bool host_dst;
   if ((rc = copy_out(obj_out, p->sc.tr_obj, sizeof(double) * 4 * n_trials, st, host_dst))) return rc;
-  // the host staging vectors die at return: wait for the uploads
-  CU(cudaStreamSynchronize(st));
+  if (host_dst) CU(cudaStreamSynchronize(st));
   p->have_partial = true;
   p->partial_safe = safe;
   p->last_ntr = n_trials;
   p->last_ntt = (int)tot;
-  p->last_cand = cid;
-  p->last_group = gid;
-  p->last_first = first;
-  p->last_ntt_v = ntt;
-  p->last_nlist = (int)cptr.size() - 1;
+  p->last_cand = L->cid;
+  p->last_group = L->gid;
+  p->last_first = L->first;
+  p->last_ntt_v = L->ntt;
+  p->last_nlist = (int)L->cptr.size() - 1;
   return DMR_OK;
 }
 
 namespace {
 
 int do_commit(dmr_problem* p, const uint8_t* d_accept) {
-  Batch b = make_batch(p, p->sc, p->last_ntt, p->last_ntr);
-  launch_commit(p->d_prob, b, d_accept, p->sc.tr_group, p->d_gptr, p->d_gpts, p->sc.cand_ptr, p->sc.cand_trials,
-                p->last_nlist, p->st);
+  Batch b = layout_batch(p, p->cur, p->last_ntr);
+  launch_commit(p->d_prob, b, d_accept, p->cur->tr_group, p->d_gptr, p->d_gpts, p->cur->cand_ptr,
+                p->cur->cand_trials, p->last_nlist, p->st);
   CU(cudaGetLastError());
   p->have_partial = false;
   return DMR_OK;
@@ -943,7 +1038,7 @@ int dmr_commit_improving(dmr_problem* p, uint8_t* accept_out) {
   if (!p) return fail(DMR_EINVAL, "null problem");
   if (!p->have_partial) return fail(DMR_ESTATE, "no partial evaluation to commit");
   if (!p->partial_safe) return fail(DMR_EINVAL, "trials of one candidate overlap; commit explicitly");
-  Batch b = make_batch(p, p->sc, p->last_ntt, p->last_ntr);
+  Batch b = layout_batch(p, p->cur, p->last_ntr);
   launch_accept(p->d_prob, b, p->sc.accept, p->st);
   int ntr = p->last_ntr;
   int rc = do_commit(p, p->sc.accept);
