@@ -175,6 +175,14 @@ int dmr_samples(dmr_problem* p, long long* samples, int reset);
 int dmr_plan_generation(dmr_problem* p, int n_cand, const int* cand_ids, const double* deltas,
                         dmr_plan** out);
 int dmr_plan_run(dmr_plan* plan);
+/* New proposal offsets for the next runs of a plan: deltas[q] for problem q
+ * of the plan (one pointer for a single-problem plan), each laid out as at
+ * plan creation, host or device memory.  Enqueued on the plan's stream
+ * before any later dmr_plan_run; a host buffer in pinned memory must stay
+ * unchanged until that run has started, pageable memory is read before the
+ * call returns.  This is how an optimiser feeds a new generation's samples
+ * into a captured plan. */
+int dmr_plan_update(dmr_plan* plan, const double* const* deltas);
 
 /* Batches of independent registration problems of uneven size (images,
  * meshes, populations): every kernel of a generation plan serves all of

@@ -239,6 +239,17 @@ struct dmr_plan {
   int* cand_ptr = nullptr;
   int* cand_trials = nullptr;
   Scratch sc;  // per-wave scratch (largest wave)
+  // dmr_plan_update: per plan trial its problem and offset in that problem's
+  // [n_groups][n_cand][2][3][G_q] deltas; staging copies of those arrays
+  int G = 1;
+  std::vector<size_t> raw_count;  // per problem
+  std::vector<int> raw_G;
+  int* slot_q = nullptr;
+  long long* slot_src = nullptr;
+  std::vector<double*> raw;       // device staging per problem
+  const double** d_raw = nullptr; // device array of the source pointers
+  int* d_rawG = nullptr;          // device array of G_q
+  int n_slots = 0;
 };
 
 // ------------------------------------------------------------ topology
@@ -1237,6 +1248,10 @@ int dmr_plan_destroy(dmr_plan* pl) {
   dfree(pl->tt_trial); dfree(pl->tt_tet); dfree(pl->tt_slot); dfree(pl->tr_cand); dfree(pl->tr_first);
   dfree(pl->tr_ntt); dfree(pl->tr_group); dfree(pl->tr_prob); dfree(pl->deltas); dfree(pl->cand_ptr);
   dfree(pl->cand_trials);
+  dfree(pl->slot_q); dfree(pl->slot_src);
+  for (double*& r : pl->raw) dfree(r);
+  if (pl->d_raw) cudaFree((void*)pl->d_raw);
+  dfree(pl->d_rawG);
   pl->sc.release();
   delete pl;
   return DMR_OK;
@@ -1265,6 +1280,8 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
   std::vector<int> tt_trial, tt_tet, tr_cand, tr_first, tr_ntt, tr_group, tr_prob, cptr, ctr;
   std::vector<uint32_t> tt_slot;
   std::vector<double> dl;
+  std::vector<int> sl_q;
+  std::vector<long long> sl_src;
   std::vector<int> w_tt0, w_ntt, w_tr0, w_ntr, w_c0, w_nlist;
   int max_tt = 0, max_tr = 0;
   const size_t dl_per = (size_t)6 * G;
@@ -1298,6 +1315,8 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
           ttw += n;
           // [2][3][Gq] of the problem -> [2][3][G] of the plan
           const double* src = &deltas[q][((size_t)g * nc + ci) * 6 * Gq];
+          sl_q.push_back(q);
+          sl_src.push_back((long long)(((size_t)g * nc + ci) * 6 * Gq));
           size_t base = dl.size();
           dl.resize(base + dl_per, 0.0);
           for (int ma = 0; ma < 6; ++ma)
@@ -1318,9 +1337,17 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
       (rc = dalloc(&pl->tr_first, tr_first.size())) || (rc = dalloc(&pl->tr_ntt, tr_ntt.size())) ||
       (rc = dalloc(&pl->tr_group, tr_group.size())) || (rc = dalloc(&pl->tr_prob, tr_prob.size())) ||
       (rc = dalloc(&pl->deltas, dl.size())) || (rc = dalloc(&pl->cand_ptr, cptr.size())) ||
-      (rc = dalloc(&pl->cand_trials, ctr.size())) || (rc = pl->sc.ensure(max_tt, max_tr, G, acap))) {
+      (rc = dalloc(&pl->cand_trials, ctr.size())) || (rc = pl->sc.ensure(max_tt, max_tr, G, acap)) ||
+      (rc = dalloc(&pl->slot_q, std::max<size_t>(1, sl_q.size()))) ||
+      (rc = dalloc(&pl->slot_src, std::max<size_t>(1, sl_src.size())))) {
     dmr_plan_destroy(pl);
     return rc;
+  }
+  pl->G = G;
+  pl->n_slots = (int)sl_q.size();
+  for (int q = 0; q < nq; ++q) {
+    pl->raw_count.push_back(deltas[q].size());
+    pl->raw_G.push_back(probs[q]->gmax);
   }
   auto up = [&](void* d, const void* h, size_t bytes) { return cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice); };
   if (up(pl->tt_trial, tt_trial.data(), 4 * tt_trial.size()) || up(pl->tt_tet, tt_tet.data(), 4 * tt_tet.size()) ||
@@ -1328,7 +1355,8 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
       up(pl->tr_first, tr_first.data(), 4 * tr_first.size()) || up(pl->tr_ntt, tr_ntt.data(), 4 * tr_ntt.size()) ||
       up(pl->tr_group, tr_group.data(), 4 * tr_group.size()) || up(pl->tr_prob, tr_prob.data(), 4 * tr_prob.size()) ||
       up(pl->deltas, dl.data(), 8 * dl.size()) || up(pl->cand_ptr, cptr.data(), 4 * cptr.size()) ||
-      up(pl->cand_trials, ctr.data(), 4 * ctr.size())) {
+      up(pl->cand_trials, ctr.data(), 4 * ctr.size()) || up(pl->slot_q, sl_q.data(), 4 * sl_q.size()) ||
+      up(pl->slot_src, sl_src.data(), 8 * sl_src.size())) {
     dmr_plan_destroy(pl);
     return fail(DMR_ECUDA, "plan upload failed");
   }
@@ -1520,6 +1548,38 @@ int dmr_batch_plan_generation(dmr_batch* bt, const int* n_cand, const int* const
     CU(cudaMemcpy(hd[q].data(), deltas[q], sizeof(double) * hd[q].size(), cudaMemcpyDefault));
   }
   return build_plan(bt->probs, bt->d_probs, bt->d_gptr, bt->d_gpts, bt->goff, cands, hd, out);
+}
+
+int dmr_plan_update(dmr_plan* pl, const double* const* deltas) {
+  if (!pl || !pl->exec || !deltas) return fail(DMR_EINVAL, "null argument");
+  const int nq = (int)pl->raw_count.size();
+  cudaStream_t st = pl->p->st;
+  if (pl->raw.empty()) {
+    pl->raw.assign(nq, nullptr);
+    for (int q = 0; q < nq; ++q) {
+      int rc = dalloc(&pl->raw[q], std::max<size_t>(1, pl->raw_count[q]));
+      if (rc) return rc;
+    }
+    CU(cudaMalloc((void**)&pl->d_raw, sizeof(double*) * nq));
+    int rc = dalloc(&pl->d_rawG, nq);
+    if (rc) return rc;
+    CU(cudaMemcpy(pl->d_rawG, pl->raw_G.data(), sizeof(int) * nq, cudaMemcpyHostToDevice));
+  }
+  std::vector<const double*> src(nq);
+  for (int q = 0; q < nq; ++q) {
+    if (!deltas[q]) return fail(DMR_EINVAL, "null deltas");
+    if (is_device_ptr(deltas[q])) {
+      src[q] = deltas[q];
+    } else {
+      CU(cudaMemcpyAsync(pl->raw[q], deltas[q], sizeof(double) * pl->raw_count[q], cudaMemcpyHostToDevice, st));
+      src[q] = pl->raw[q];
+    }
+  }
+  // pageable host memory: both copies are staged before the calls return
+  CU(cudaMemcpyAsync((void*)pl->d_raw, src.data(), sizeof(double*) * nq, cudaMemcpyHostToDevice, st));
+  launch_gather_deltas(pl->d_raw, pl->slot_q, pl->slot_src, pl->d_rawG, pl->n_slots, pl->G, pl->deltas, st);
+  CU(cudaGetLastError());
+  return DMR_OK;
 }
 
 int dmr_plan_run(dmr_plan* pl) {

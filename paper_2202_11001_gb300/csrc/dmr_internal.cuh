@@ -130,6 +130,8 @@ void launch_build_cells(const void* plain, int dtype, const int n[3], void* cell
                         unsigned long long* cmask, cudaStream_t st);
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
 void launch_refine(const double* coarse, int n_cand, const int m[3], double* fine, cudaStream_t st);
+void launch_gather_deltas(const double* const* raw, const int* slot_q, const long long* slot_src, const int* raw_G,
+                          int n_slots, int G, double* out, cudaStream_t st);
 // Raster kernels: fast pass, then the full-logic pass over the items it
 // handed over.  With a side stream, `fork` is recorded on `st` after the fast
 // pass and the side stream waits on it (work placed there runs beside the

@@ -476,6 +476,25 @@ void launch_refine(const double* coarse, int n_cand, const int m[3], double* fin
   k_refine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(coarse, n_cand, d, fine);
 }
 
+// Plan deltas from the caller's per-problem [n_groups][n_cand][2][3][G_q]
+// arrays into the plan's trial order [slot][2][3][G] (zero beyond G_q).
+__global__ void k_gather_deltas(const double* const* raw, const int* slot_q, const long long* slot_src,
+                                const int* raw_G, int n_slots, int G, double* out) {
+  const long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (id >= (long)n_slots * 6 * G) return;
+  const long k = id / (6 * G);
+  const int r = (int)(id % (6 * G)), ma = r / G, j = r % G;
+  const int q = slot_q[k], Gq = raw_G[q];
+  out[id] = j < Gq ? raw[q][slot_src[k] + (long)ma * Gq + j] : 0.0;
+}
+
+void launch_gather_deltas(const double* const* raw, const int* slot_q, const long long* slot_src, const int* raw_G,
+                          int n_slots, int G, double* out, cudaStream_t st) {
+  const long n = (long)n_slots * 6 * G;
+  if (n <= 0) return;
+  k_gather_deltas<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(raw, slot_q, slot_src, raw_G, n_slots, G, out);
+}
+
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st) {
   if (b.n_tt <= 0) return;
   k_setup<<<(b.n_tt + 127) / 128, 128, 0, st>>>(probs, b);

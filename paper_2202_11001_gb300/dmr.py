@@ -80,6 +80,7 @@ def load():
         "dmr_samples": [vp, ctypes.POINTER(ctypes.c_longlong), i],
         "dmr_plan_generation": [vp, i, vp, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_plan_run": [vp],
+        "dmr_plan_update": [vp, vp],
         "dmr_plan_destroy": [vp],
         "dmr_plan_launches": [vp, ip],
         "dmr_plan_kernel_ms": [vp, ip, ip],
@@ -115,7 +116,7 @@ def exported_symbols():
         "dmr_problem_create", "dmr_problem_destroy", "dmr_set_stream", "dmr_problem_info", "dmr_tets_out",
         "dmr_set_fos", "dmr_fos_info", "dmr_fos_waves", "dmr_eval_full", "dmr_eval_partial", "dmr_commit",
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
-        "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_destroy",
+        "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_update", "dmr_plan_destroy",
         "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_batch_create", "dmr_batch_destroy",
         "dmr_batch_plan_generation", "dmr_hypervolume", "dmr_refine", "dmr_mlp_create", "dmr_mlp_destroy", "dmr_mlp_n_params",
         "dmr_mlp_params", "dmr_mlp_features", "dmr_mlp_forward", "dmr_mlp_train_step", "dmr_eval_one_noalloc", "dmr_last_error",
@@ -467,6 +468,16 @@ class Plan:
 
     def run(self):
         _check(self.prob._lib.dmr_plan_run(self.h))
+
+    def update(self, deltas):
+        """New proposal offsets for later runs: one array (single problem) or
+        a list with one per problem, laid out as at plan creation; numpy or
+        torch (host or device)."""
+        arrs = deltas if isinstance(deltas, (list, tuple)) else [deltas]
+        args = [_Arg(a, np.float64) for a in arrs]
+        ptrs = (ctypes.c_void_p * len(args))(*[a.ptr for a in args])
+        self._keep = args
+        _check(self.prob._lib.dmr_plan_update(self.h, ctypes.addressof(ptrs)))
 
     def kernel_ms(self):
         """(set-up ms, raster ms) of the last completed run."""

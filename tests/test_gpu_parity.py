@@ -231,3 +231,34 @@ def test_batched_problems_equal_single_plans_and_oracle():
         for c in range(C):
             assert np.array_equal(final[c], gs.coords(c))
         assert_obj_close(gb.objectives(), o.eval_full(final))
+
+
+def test_plan_update_equals_new_plan():
+    """dmr_plan_update: a plan fed new proposal offsets (host or device) runs
+    exactly like a plan built with them."""
+    import torch
+
+    pr = synth.sphere_pair(seed=40, C=5)
+    C = 5
+    g1, _ = make_pair(pr)
+    g2, _ = make_pair(pr)
+    groups = synth.single_point_fos(pr["mesh"])
+    for g in (g1, g2):
+        g.eval_full(pr["coords"])
+        g.set_fos(groups)
+    d0 = _deltas(pr, groups, C, 0.3, 41)
+    d1 = _deltas(pr, groups, C, 0.3, 42)
+    d2 = _deltas(pr, groups, C, 0.3, 43)
+    p1 = g1.plan_generation(np.arange(C, dtype=np.int32), d0)
+    p2 = g2.plan_generation(np.arange(C, dtype=np.int32), d1)
+    p1.update(d1)
+    p1.run()
+    p2.run()
+    assert np.array_equal(g1.objectives(), g2.objectives())
+    p1.update(torch.from_numpy(d2).cuda())
+    p3 = g2.plan_generation(np.arange(C, dtype=np.int32), d2)
+    p1.run()
+    p3.run()
+    assert np.array_equal(g1.objectives(), g2.objectives())
+    for c in range(C):
+        assert np.array_equal(g1.coords(c), g2.coords(c))
