@@ -555,41 +555,38 @@ __device__ __forceinline__ bool vol_positive(const ItemRec& r) {
   return v > 0 && isfinite(v);
 }
 
-// Squared physical distance of a mapped guidance point pm (in the partner
-// image of mesh `mesh`) from partner point q, in the partner's spacing.
-__device__ __forceinline__ double landmark_dist2(const DevProblem& pr, const double pm[3], const double* q, int mesh) {
-  const int dp = 1 - mesh;
-  double s = 0.0;
-  for (int a = 0; a < 3; ++a) {
-    const double d = dmul(dsub(pm[a], q[a]), pr.spd[dp][a]);
-    s = dadd(s, dmul(d, d));
-  }
-  return s;
-}
-
 // Sec. 2.3.3: smallest squared physical distance between guidance point i
 // of mesh `mesh` (at p), mapped through the record's tet, and the partner
-// points of its set (its own partner when there are no sets).
+// points of its set (its own partner when there are no sets).  The mapped
+// point is p + disp with disp = d0 + G (p - own_0) small, so the distance
+// vector (p - q) + disp is formed from the FP64 differences p - own_0,
+// d0 and p - q rounded once to FP32 and the FP32 map: a few 1e-7 of the
+// distance, with a dozen FP64 operations instead of ~40 (this runs on one
+// lane, and an FP64 instruction occupies the pipe for the whole warp).
 __device__ double landmark_term(const ItemRec& r, const DevProblem& pr, const double p[3], int mesh, int i) {
-  // mapped landmark (v + d0) + G (v - own_0) with the record's FP64 map
-  double pm[3];
+  float u[3], disp[3];
+  for (int a = 0; a < 3; ++a) u[a] = (float)dsub(p[a], r.X[0][a]);
   for (int c = 0; c < 3; ++c)
-    pm[c] = (p[c] + (r.XP[0][c] - r.X[0][c])) +
-            fma(r.Gd[c][0], p[0] - r.X[0][0], fma(r.Gd[c][1], p[1] - r.X[0][1], r.Gd[c][2] * (p[2] - r.X[0][2])));
+    disp[c] = (float)dsub(r.XP[0][c], r.X[0][c]) + fmaf(r.G[c][0], u[0], fmaf(r.G[c][1], u[1], r.G[c][2] * u[2]));
+  const int dp = 1 - mesh;
   int k0 = 0, k1 = 1;
   if (pr.gsid) {
     const int s = pr.gsid[i];
     k0 = pr.gptr[s];
     k1 = pr.gptr[s + 1];
   }
-  double best = INFINITY;
+  float best = INFINITY;
   for (int k = k0; k < k1; ++k) {
     const int j = pr.gsid ? pr.gmem[k] : i;
     const double* q = pr.guide + 6 * j + 3 * (1 - mesh);
-    const double t = landmark_dist2(pr, pm, q, mesh);
+    float t = 0.f;
+    for (int a = 0; a < 3; ++a) {
+      const float d = ((float)dsub(p[a], q[a]) + disp[a]) * pr.sp[dp][a];
+      t = fmaf(d, d, t);
+    }
     best = t < best ? t : best;
   }
-  return best;
+  return (double)best;
 }
 
 // Test one tet record for landmark p: volume sign first (folded tets never

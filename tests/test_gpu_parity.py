@@ -26,7 +26,7 @@ def test_full_sphere16(model):
         lg, tg = g.landmarks(c)
         lo, to = o.landmarks(c)
         assert np.array_equal(lg, lo)
-        assert np.allclose(tg, to, rtol=1e-12, atol=1e-15)
+        assert np.allclose(tg, to, rtol=RTOL, atol=1e-12)
 
 
 def test_regular_mesh_ties_bit_exact():
