@@ -239,6 +239,16 @@ int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, flo
  * enqueued on the problem's stream; the call does not wait for it. */
 int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double* obj_out);
 
+/* The paper's folding check (Sec. 2.3.4), as a cross-check of the signed
+ * volumes that c_fold counts: per candidate and mesh, the number of points
+ * of the committed coordinates that lie outside their link (the faces of
+ * their star's tets that do not contain them), by the parity of the
+ * crossings of a fixed ray (Moeller-Trumbore triangle test); border points
+ * in their border plane against the polygon of the star's in-plane edges;
+ * border-edge points between their two neighbours along the free axis.
+ * cand_ids [n_cand] host or device; out [n_cand][2] host or device. */
+int dmr_link_check(dmr_problem* p, int n_cand, const int* cand_ids, int* out);
+
 /* Grid refinement for the multi-resolution scheme (Sec. 2.4): every cube
  * cell of both meshes gains a point in the middle of each edge, in the
  * middle of each face and at its centre, so m[a] points per axis become

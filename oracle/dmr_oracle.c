@@ -1111,3 +1111,132 @@ int dmo_refine(const double* coarse, int ncand, int mx, int my, int mz, double* 
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------ link test
+ * The paper's folding check (Sec. 2.3.4): a point violates the constraint if
+ * it lies outside the polyhedron formed by the faces of its star's tets that
+ * do not contain it (its link).  Inside / outside by the parity of the
+ * crossings of a ray from the point.  Border points (one fixed axis) move in
+ * their border plane and are tested in 2-D against the polygon of the star
+ * triangles' edges that lie in that plane; points on a border edge (two fixed
+ * axes) must lie strictly between their two lattice neighbours along the free
+ * axis; corners are fixed.
+ * Ray directions: (1, RAY_Y, RAY_Z) in 3-D and (1, RAY_Y) over the two free
+ * axes (in axis order) in 2-D, fixed "generic" constants so that a ray meets a
+ * triangle edge or a segment end only on a set of measure zero.  Triangle
+ * crossing (Moeller & Trumbore, "Fast, minimum storage ray-triangle
+ * intersection", 1997): closed triangle, strictly ahead of the origin.
+ * Segment crossing: segment parameter in [0, 1), strictly ahead.  FP64, one
+ * rounding per operation in the order written. */
+#define RAY_Y 0.7548776662466927
+#define RAY_Z 0.5698402909980532
+
+static int ray_hits_triangle(const double* o, const double* a, const double* b, const double* c) {
+  const double R[3] = {1.0, RAY_Y, RAY_Z};
+  double e1[3], e2[3], tv[3], pv[3], qv[3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = b[k] - a[k];
+    e2[k] = c[k] - a[k];
+    tv[k] = o[k] - a[k];
+  }
+  pv[0] = R[1] * e2[2] - R[2] * e2[1];
+  pv[1] = R[2] * e2[0] - R[0] * e2[2];
+  pv[2] = R[0] * e2[1] - R[1] * e2[0];
+  const double det = (e1[0] * pv[0] + e1[1] * pv[1]) + e1[2] * pv[2];
+  if (det == 0.0) return 0;
+  const double inv = 1.0 / det;
+  const double u = ((tv[0] * pv[0] + tv[1] * pv[1]) + tv[2] * pv[2]) * inv;
+  if (u < 0.0 || u > 1.0) return 0;
+  qv[0] = tv[1] * e1[2] - tv[2] * e1[1];
+  qv[1] = tv[2] * e1[0] - tv[0] * e1[2];
+  qv[2] = tv[0] * e1[1] - tv[1] * e1[0];
+  const double w = ((R[0] * qv[0] + R[1] * qv[1]) + R[2] * qv[2]) * inv;
+  if (w < 0.0 || u + w > 1.0) return 0;
+  const double t = ((e2[0] * qv[0] + e2[1] * qv[1]) + e2[2] * qv[2]) * inv;
+  return t > 0.0;
+}
+
+/* 2-D: ray o + s (1, RAY_Y), s > 0, against segment p + r (q - p), 0 <= r < 1 */
+static int ray_hits_segment(const double* o, const double* p, const double* q) {
+  const double dx = q[0] - p[0], dy = q[1] - p[1];
+  const double den = 1.0 * dy - RAY_Y * dx;
+  if (den == 0.0) return 0;
+  const double px = p[0] - o[0], py = p[1] - o[1];
+  const double s = (px * dy - py * dx) / den;
+  const double r = (px * RAY_Y - py * 1.0) / den;
+  return s > 0.0 && r >= 0.0 && r < 1.0;
+}
+
+static int lattice_index(const int* m, int v, int ax) {
+  return ax == 0 ? v % m[0] : ax == 1 ? (v / m[0]) % m[1] : v / (m[0] * m[1]);
+}
+
+/* 1 if point v of mesh `mesh` (coords c = [2][3][P]) violates its link */
+static int link_violation(const dmo_problem* pr, const double* c, int mesh, int v) {
+  const int P = pr->P;
+  const double* X = c + (size_t)mesh * 3 * P;
+  const uint8_t fm = pr->fixmask[v];
+  const int nfix = (fm & 1) + ((fm >> 1) & 1) + ((fm >> 2) & 1);
+  double o[3] = {X[v], X[P + v], X[2 * P + v]};
+  if (nfix == 3) return 0;
+  if (nfix == 2) {
+    const int ax = !(fm & 1) ? 0 : !(fm & 2) ? 1 : 2;
+    const int step = ax == 0 ? 1 : ax == 1 ? pr->m[0] : pr->m[0] * pr->m[1];
+    const double lo = X[(size_t)ax * P + v - step], hi = X[(size_t)ax * P + v + step];
+    return !(lo < o[ax] && o[ax] < hi);
+  }
+  int hits = 0;
+  if (nfix == 0) {
+    for (int s = pr->star_ptr[v]; s < pr->star_ptr[v + 1]; ++s) {
+      const int t = pr->star[s];
+      double V[3][3];
+      int n = 0;
+      for (int i = 0; i < 4; ++i) {
+        const int w = pr->tet[4 * t + i];
+        if (w == v) continue;
+        for (int a = 0; a < 3; ++a) V[n][a] = X[(size_t)a * P + w];
+        ++n;
+      }
+      hits += ray_hits_triangle(o, V[0], V[1], V[2]);
+    }
+    return !(hits & 1);
+  }
+  /* one fixed axis f: the star triangles lying in v's border plane */
+  const int f = (fm & 1) ? 0 : (fm & 2) ? 1 : 2;
+  const int a1 = f == 0 ? 1 : 0, a2 = f == 2 ? 1 : 2;
+  const int fv = lattice_index(pr->m, v, f);
+  const double o2[2] = {o[a1], o[a2]};
+  for (int s = pr->star_ptr[v]; s < pr->star_ptr[v + 1]; ++s) {
+    const int t = pr->star[s];
+    int ids[2], n = 0, ok = 1;
+    for (int i = 0; i < 4; ++i) {
+      const int w = pr->tet[4 * t + i];
+      if (w == v) continue;
+      if (lattice_index(pr->m, w, f) == fv) {
+        if (n < 2) ids[n] = w;
+        ++n;
+      }
+    }
+    if (n != 2) ok = 0;
+    if (!ok) continue;
+    const double p[2] = {X[(size_t)a1 * P + ids[0]], X[(size_t)a2 * P + ids[0]]};
+    const double q[2] = {X[(size_t)a1 * P + ids[1]], X[(size_t)a2 * P + ids[1]]};
+    hits += ray_hits_segment(o2, p, q);
+  }
+  return !(hits & 1);
+}
+
+/* 1 if point v of `mesh` lies outside its link */
+int dmo_link_point(void* h, const double* coords, int mesh, int v) {
+  return link_violation((const dmo_problem*)h, coords, mesh, v);
+}
+
+/* out2[mesh] = number of points of that mesh outside their link */
+void dmo_link_violations(void* h, const double* coords, int32_t* out2) {
+  const dmo_problem* pr = (const dmo_problem*)h;
+  for (int mesh = 0; mesh < 2; ++mesh) {
+    int n = 0;
+    for (int v = 0; v < pr->P; ++v) n += link_violation(pr, coords, mesh, v);
+    out2[mesh] = n;
+  }
+}

@@ -59,6 +59,8 @@ def _load():
                                    ctypes.c_double]
         lib.dmo_destroy.argtypes = [vp]
         lib.dmo_set_guide_sets.argtypes = [vp, ctypes.c_void_p]
+        lib.dmo_link_violations.argtypes = [vp, _f64p, _i32p]
+        lib.dmo_link_point.argtypes = [vp, _f64p, ctypes.c_int, ctypes.c_int]
         lib.dmo_ntet.argtypes = [vp]
         lib.dmo_npoints.argtypes = [vp]
         lib.dmo_get_tets.argtypes = [vp, _i32p]
@@ -285,6 +287,16 @@ class Oracle:
         b = ctypes.c_int32(0)
         s = self._lib.dmo_sample(self.h, int(img), _f64(p), ctypes.byref(b))
         return s, bool(b.value)
+
+    def link_violations(self, coords1):
+        """Points outside their link per mesh (Sec. 2.3.4 ray test), [2]."""
+        out = np.zeros(2, np.int32)
+        self._lib.dmo_link_violations(self.h, _f64(coords1).reshape(-1), out)
+        return out
+
+    def link_point(self, coords1, mesh, v):
+        """1 when point v of `mesh` lies outside its link (Sec. 2.3.4)."""
+        return int(self._lib.dmo_link_point(self.h, _f64(coords1).reshape(-1), int(mesh), int(v)))
 
     def six_vol(self, mesh, coords1, t):
         return float(self._lib.dmo_six_vol(self.h, int(mesh), _f64(coords1).reshape(-1), int(t)))

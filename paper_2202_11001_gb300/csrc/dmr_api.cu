@@ -183,6 +183,8 @@ struct dmr_problem {
   int4* d_tet = nullptr;
   uint32_t* d_fperm = nullptr;
   uint8_t* d_fix = nullptr;
+  int* d_star_ptr = nullptr;
+  int* d_star = nullptr;
   float* d_restvol = nullptr;
   double* d_guide = nullptr;
   std::vector<int> gs_id, gs_ptr, gs_mem;  // guidance sets (empty: one set per pair)
@@ -349,6 +351,7 @@ void release_problem(dmr_problem* p) {
     dfree(p->cmask[k]);
   }
   dfree(p->d_tet); dfree(p->d_fperm); dfree(p->d_fix); dfree(p->d_restvol); dfree(p->d_guide);
+  dfree(p->d_star_ptr); dfree(p->d_star);
   dfree(p->d_gs_id); dfree(p->d_gs_ptr); dfree(p->d_gs_mem);
   dfree(p->d_coords); dfree(p->d_ssd); dfree(p->d_cov); dfree(p->d_def); dfree(p->d_fold);
   dfree(p->d_loc); dfree(p->d_gterm); dfree(p->d_sums); dfree(p->d_samples); dfree(p->d_prob); dfree(p->d_obj);
@@ -517,6 +520,10 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       rvs += std::fabs(det) / 6.0;
     }
     size_t C = p->cap;
+    if ((rc = dalloc(&p->d_star_ptr, p->star_ptr.size())) || (rc = dalloc(&p->d_star, p->star.size())))
+      goto fail_;
+    cudaMemcpyAsync(p->d_star_ptr, p->star_ptr.data(), sizeof(int) * p->star_ptr.size(), cudaMemcpyHostToDevice, p->st);
+    cudaMemcpyAsync(p->d_star, p->star.data(), sizeof(int) * p->star.size(), cudaMemcpyHostToDevice, p->st);
     if ((rc = dalloc(&p->d_tet, p->ntet)) || (rc = dalloc(&p->d_fperm, p->ntet)) || (rc = dalloc(&p->d_fix, p->P)) ||
         (rc = dalloc(&p->d_restvol, p->ntet)) || (rc = dalloc(&p->d_guide, std::max<size_t>(1, p->guide.size()))) ||
         (rc = dalloc(&p->d_coords, C * 6 * p->P)) || (rc = dalloc(&p->d_ssd, C * p->ntet * 2)) ||
@@ -560,6 +567,8 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
     h.tet = p->d_tet;
     h.fperm = p->d_fperm;
     h.fixmask = p->d_fix;
+    h.star_ptr = p->d_star_ptr;
+    h.star = p->d_star;
     h.rest_vol = p->d_restvol;
     h.black_rule = p->black_rule;
     h.model = p->model;
@@ -1125,6 +1134,33 @@ int dmr_trial_out(dmr_problem* p, int k, int* tets, int* cov, double* ssd, doubl
   if (def) CU(cudaMemcpy(def, p->sc.o_def + f, sizeof(double) * n, cudaMemcpyDefault));
   if (fold) CU(cudaMemcpy(fold, p->sc.o_fold + f, sizeof(int) * n, cudaMemcpyDefault));
   return n;
+}
+
+int dmr_link_check(dmr_problem* p, int n_cand, const int* cand_ids, int* out) {
+  if (!p || !cand_ids || !out) return fail(DMR_EINVAL, "null argument");
+  if (n_cand < 1 || n_cand > p->C) return fail(DMR_EINVAL, "n_cand out of range");
+  std::vector<int> cid(n_cand);
+  if (is_device_ptr(cand_ids)) CU(cudaMemcpy(cid.data(), cand_ids, sizeof(int) * n_cand, cudaMemcpyDeviceToHost));
+  else std::memcpy(cid.data(), cand_ids, sizeof(int) * n_cand);
+  for (int c : cid)
+    if (c < 0 || c >= p->C) return fail(DMR_EINVAL, "candidate id out of range");
+  int* d_c = nullptr;
+  int* d_out = nullptr;
+  int rc;
+  if ((rc = dalloc(&d_c, n_cand)) || (rc = dalloc(&d_out, 2 * (size_t)n_cand))) {
+    dfree(d_c);
+    return rc;
+  }
+  cudaMemcpyAsync(d_c, cid.data(), sizeof(int) * n_cand, cudaMemcpyHostToDevice, p->st);
+  cudaMemsetAsync(d_out, 0, sizeof(int) * 2 * n_cand, p->st);
+  launch_link_check(p->d_prob, p->hp, d_c, n_cand, d_out, p->st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(int) * 2 * n_cand, cudaMemcpyDefault, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  dfree(d_c);
+  dfree(d_out);
+  if (e != cudaSuccess) return fail(DMR_ECUDA, std::string("link check: ") + cudaGetErrorString(e));
+  return DMR_OK;
 }
 
 int dmr_refine(const double* coarse, int n_cand, const int* m, double* fine, void* stream) {

@@ -38,6 +38,8 @@ struct DevProblem {
   const int4* tet;          // [ntet] point ids, positive rest orientation
   const uint32_t* fperm;    // [ntet] 4 faces x 8 bits: a|b<<2|c<<4|neg<<6
   const uint8_t* fixmask;   // [P] bit a: axis a fixed; bit 3+a: upper border
+  const int* star_ptr;      // [P+1] point -> tets CSR
+  const int* star;          // [4 ntet]
   const float* rest_vol;    // [ntet] source rest volume (mm^3), LINEAR model
   int black_rule, model;
   float lam, mu;
@@ -130,6 +132,8 @@ void launch_build_cells(const void* plain, int dtype, const int n[3], void* cell
                         unsigned long long* cmask, cudaStream_t st);
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
 void launch_refine(const double* coarse, int n_cand, const int m[3], double* fine, cudaStream_t st);
+void launch_link_check(const DevProblem* probs, const DevProblem& hp, const int* cands, int n_cand, int* out,
+                       cudaStream_t st);
 void launch_gather_deltas(const double* const* raw, const int* slot_q, const long long* slot_src, const int* raw_G,
                           int n_slots, int G, double* out, cudaStream_t st);
 // Raster kernels: fast pass, then the full-logic pass over the items it

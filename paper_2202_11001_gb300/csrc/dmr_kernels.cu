@@ -476,6 +476,123 @@ void launch_refine(const double* coarse, int n_cand, const int m[3], double* fin
   k_refine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(coarse, n_cand, d, fine);
 }
 
+// ------------------------------------------------------------ link test
+// The paper's folding check (Sec. 2.3.4): a point is outside its link (the
+// faces of its star's tets that do not contain it) when a ray from it
+// crosses the link an even number of times; border points in their plane
+// against the star triangles' edges there (2-D), border-edge points between
+// their two neighbours along the free axis, corners never.  Ray directions
+// (1, kRayY, kRayZ) and (1, kRayY) over the two free axes; triangle crossing
+// after Moeller & Trumbore (1997), closed triangle, strictly ahead; segment
+// parameter in [0, 1).  FP64 with one rounding per operation, in the
+// oracle's order, so the counts equal the oracle's.
+constexpr double kRayY = 0.7548776662466927, kRayZ = 0.5698402909980532;
+
+__device__ int ray_hits_triangle(const double* o, const double* a, const double* b, const double* c) {
+  const double R[3] = {1.0, kRayY, kRayZ};
+  double e1[3], e2[3], tv[3], pv[3], qv[3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = dsub(b[k], a[k]);
+    e2[k] = dsub(c[k], a[k]);
+    tv[k] = dsub(o[k], a[k]);
+  }
+  pv[0] = dsub(dmul(R[1], e2[2]), dmul(R[2], e2[1]));
+  pv[1] = dsub(dmul(R[2], e2[0]), dmul(R[0], e2[2]));
+  pv[2] = dsub(dmul(R[0], e2[1]), dmul(R[1], e2[0]));
+  const double det = dadd(dadd(dmul(e1[0], pv[0]), dmul(e1[1], pv[1])), dmul(e1[2], pv[2]));
+  if (det == 0.0) return 0;
+  const double inv = __ddiv_rn(1.0, det);
+  const double u = dmul(dadd(dadd(dmul(tv[0], pv[0]), dmul(tv[1], pv[1])), dmul(tv[2], pv[2])), inv);
+  if (u < 0.0 || u > 1.0) return 0;
+  qv[0] = dsub(dmul(tv[1], e1[2]), dmul(tv[2], e1[1]));
+  qv[1] = dsub(dmul(tv[2], e1[0]), dmul(tv[0], e1[2]));
+  qv[2] = dsub(dmul(tv[0], e1[1]), dmul(tv[1], e1[0]));
+  const double w = dmul(dadd(dadd(dmul(R[0], qv[0]), dmul(R[1], qv[1])), dmul(R[2], qv[2])), inv);
+  if (w < 0.0 || dadd(u, w) > 1.0) return 0;
+  const double t = dmul(dadd(dadd(dmul(e2[0], qv[0]), dmul(e2[1], qv[1])), dmul(e2[2], qv[2])), inv);
+  return t > 0.0;
+}
+
+__device__ int ray_hits_segment(const double* o, const double* p, const double* q) {
+  const double dx = dsub(q[0], p[0]), dy = dsub(q[1], p[1]);
+  const double den = dsub(dmul(1.0, dy), dmul(kRayY, dx));
+  if (den == 0.0) return 0;
+  const double px = dsub(p[0], o[0]), py = dsub(p[1], o[1]);
+  const double s = __ddiv_rn(dsub(dmul(px, dy), dmul(py, dx)), den);
+  const double r = __ddiv_rn(dsub(dmul(px, kRayY), dmul(py, 1.0)), den);
+  return s > 0.0 && r >= 0.0 && r < 1.0;
+}
+
+__device__ __forceinline__ int lattice_index(const int* m, int v, int ax) {
+  return ax == 0 ? v % m[0] : ax == 1 ? (v / m[0]) % m[1] : v / (m[0] * m[1]);
+}
+
+__global__ void k_link_check(const DevProblem* __restrict__ probs, const int* __restrict__ cands, int n_cand,
+                             int* out) {
+  const DevProblem& pr = probs[0];
+  const int P = pr.P;
+  const long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (id >= (long)n_cand * 2 * P) return;
+  const int k = (int)(id / (2L * P)), mesh = (int)((id / P) % 2), v = (int)(id % P);
+  const double* X = pr.coords + ((size_t)cands[k] * 2 + mesh) * 3 * P;
+  const uint8_t fm = pr.fixmask[v];
+  const int nfix = (fm & 1) + ((fm >> 1) & 1) + ((fm >> 2) & 1);
+  const double o[3] = {X[v], X[P + v], X[2 * (size_t)P + v]};
+  int outside = 0;
+  if (nfix == 2) {
+    const int ax = !(fm & 1) ? 0 : !(fm & 2) ? 1 : 2;
+    const int step = ax == 0 ? 1 : ax == 1 ? pr.m[0] : pr.m[0] * pr.m[1];
+    const double lo = X[(size_t)ax * P + v - step], hi = X[(size_t)ax * P + v + step];
+    outside = !(lo < o[ax] && o[ax] < hi);
+  } else if (nfix == 0) {
+    int hits = 0;
+    for (int s = pr.star_ptr[v]; s < pr.star_ptr[v + 1]; ++s) {
+      const int4 tv = pr.tet[pr.star[s]];
+      const int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+      double V[3][3];
+      int n = 0;
+      for (int i = 0; i < 4; ++i) {
+        if (ids[i] == v) continue;
+        for (int a = 0; a < 3; ++a) V[n][a] = X[(size_t)a * P + ids[i]];
+        ++n;
+      }
+      hits += ray_hits_triangle(o, V[0], V[1], V[2]);
+    }
+    outside = !(hits & 1);
+  } else if (nfix == 1) {
+    const int f = (fm & 1) ? 0 : (fm & 2) ? 1 : 2;
+    const int a1 = f == 0 ? 1 : 0, a2 = f == 2 ? 1 : 2;
+    const int fv = lattice_index(pr.m, v, f);
+    const double o2[2] = {o[a1], o[a2]};
+    int hits = 0;
+    for (int s = pr.star_ptr[v]; s < pr.star_ptr[v + 1]; ++s) {
+      const int4 tv = pr.tet[pr.star[s]];
+      const int ids4[4] = {tv.x, tv.y, tv.z, tv.w};
+      int ids[2] = {0, 0}, n = 0;
+      for (int i = 0; i < 4; ++i) {
+        if (ids4[i] == v) continue;
+        if (lattice_index(pr.m, ids4[i], f) == fv) {
+          if (n < 2) ids[n] = ids4[i];
+          ++n;
+        }
+      }
+      if (n != 2) continue;
+      const double p[2] = {X[(size_t)a1 * P + ids[0]], X[(size_t)a2 * P + ids[0]]};
+      const double q[2] = {X[(size_t)a1 * P + ids[1]], X[(size_t)a2 * P + ids[1]]};
+      hits += ray_hits_segment(o2, p, q);
+    }
+    outside = !(hits & 1);
+  }
+  if (outside) atomicAdd(out + 2 * k + mesh, 1);
+}
+
+void launch_link_check(const DevProblem* probs, const DevProblem& hp, const int* cands, int n_cand, int* out,
+                       cudaStream_t st) {
+  const long n = (long)n_cand * 2 * hp.P;
+  if (n <= 0) return;
+  k_link_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(probs, cands, n_cand, out);
+}
+
 // Plan deltas from the caller's per-problem [n_groups][n_cand][2][3][G_q]
 // arrays into the plan's trial order [slot][2][3][G] (zero beyond G_q).
 __global__ void k_gather_deltas(const double* const* raw, const int* slot_q, const long long* slot_src,

@@ -92,6 +92,7 @@ def load():
         "dmr_batch_plan_generation": [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_hypervolume": [vp, i, i, vp, vp],
         "dmr_refine": [vp, i, vp, vp, vp],
+        "dmr_link_check": [vp, i, vp, vp],
         "dmr_mlp_create": [ctypes.c_ulonglong, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_mlp_destroy": [vp],
         "dmr_mlp_n_params": [],
@@ -118,7 +119,7 @@ def exported_symbols():
         "dmr_commit_improving", "dmr_objectives_out", "dmr_coords_out", "dmr_terms_out", "dmr_landmarks_out",
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_update", "dmr_plan_destroy",
         "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_batch_create", "dmr_batch_destroy",
-        "dmr_batch_plan_generation", "dmr_hypervolume", "dmr_refine", "dmr_mlp_create", "dmr_mlp_destroy", "dmr_mlp_n_params",
+        "dmr_batch_plan_generation", "dmr_hypervolume", "dmr_refine", "dmr_link_check", "dmr_mlp_create", "dmr_mlp_destroy", "dmr_mlp_n_params",
         "dmr_mlp_params", "dmr_mlp_features", "dmr_mlp_forward", "dmr_mlp_train_step", "dmr_eval_one_noalloc", "dmr_last_error",
     ]
 
@@ -366,6 +367,13 @@ class Problem:
         cands = np.arange(self.C, dtype=np.int32) if cands is None else np.asarray(cands, np.int32)
         out = np.zeros((len(cands), 4), np.float64)
         _check(self._lib.dmr_objectives_out(self.h, len(cands), cands.ctypes.data, out.ctypes.data))
+        return out
+
+    def link_check(self, cands=None):
+        """Points outside their link per (candidate, mesh), [n, 2] (Sec. 2.3.4)."""
+        cands = np.arange(self.C, dtype=np.int32) if cands is None else np.asarray(cands, np.int32)
+        out = np.zeros((len(cands), 2), np.int32)
+        _check(self._lib.dmr_link_check(self.h, len(cands), cands.ctypes.data, out.ctypes.data))
         return out
 
     def coords(self, c):
