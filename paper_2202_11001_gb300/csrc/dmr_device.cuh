@@ -288,6 +288,102 @@ static __device__ __forceinline__ void row_span(const ItemRec& r, uint32_t fp, i
   }
 }
 
+// The faces of an item sorted by the sign of A.x: "low" faces (A.x > 0)
+// bound a row from below, "high" faces (A.x < 0) from above, and faces with
+// A.x == 0 (or NaN) are constant along a row.  order holds the face ids in
+// that order, 2 bits each; shape = (number of low faces) | (number of high
+// faces) << 4 (0x13: three low faces and one high face).
+static __device__ __forceinline__ void face_order(const ItemRec& r, int& order, int& shape) {
+  int lo_ids = 0, hi_ids = 0, z_ids = 0, nl = 0, nh = 0, nz = 0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const float ax = r.fa[f][0];
+    if (ax > 0.f) {
+      lo_ids |= f << (2 * nl);
+      ++nl;
+    } else if (ax < 0.f) {
+      hi_ids |= f << (2 * nh);
+      ++nh;
+    } else {
+      z_ids |= f << (2 * nz);
+      ++nz;
+    }
+  }
+  order = lo_ids | (hi_ids << (2 * nl)) | (z_ids << (2 * (nl + nh)));
+  shape = nl | (nh << 4);
+}
+
+static __device__ __forceinline__ float2 lds2(const float* p) {
+  float2 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+
+// row_span for an item whose faces are sorted (face_order), NL low and NH
+// high faces: the same span and the same certification without tracking a
+// binding face.  h = fl(A.x x + c) is non-decreasing in x for a low face and
+// non-increasing for a high one, and |h - H| <= mu at every voxel of the box
+// (H: the FP64 predicate), so: h(lo) > mu on every low face and h(hi) > mu on
+// every high face put all of [lo, hi] inside; h(lo - 1) < -mu on some low
+// face puts every voxel left of lo outside, h(hi + 1) < -mu on some high face
+// every voxel right of hi.  A constant face with c < -mu empties the row.
+template <int NL, int NH>
+static __device__ __forceinline__ void row_span_sorted(const ItemRec& r, int order, int xl, int xh, int yi, int zi,
+                                                       int& lo, int& hi, bool& careful) {
+  constexpr int NF = NL + NH;
+  const float yr = (float)yi, zr = (float)zi;
+  const float tlo = (float)(xl - 1), thi = (float)(xh + 1);
+  float A[4], c[4], m[4];
+  lo = xl;
+  hi = xh;
+  bool ok = true, zout = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int f = (order >> (2 * i)) & 3;
+    const float4 a = lds4(&r.fa[f][0]);
+    const float2 mm = lds2(&r.fm[f][0]);
+    A[i] = a.x;
+    c[i] = fmaf(a.y, yr, fmaf(a.z, zr, a.w));
+    m[i] = mm.x;
+    if (i < NF) {
+      const float th = fminf(fmaxf(-c[i] * mm.y, tlo), thi);
+      int kb;
+      (void)ffloor_magic(th, kb);
+      if (i < NL)
+        lo = max(lo, kb - (MAGIC_BITS - 1));
+      else
+        hi = min(hi, kb - MAGIC_BITS);
+    } else {
+      zout = zout || c[i] < -m[i];
+      ok = ok && (c[i] > m[i] || c[i] < -m[i]);
+    }
+  }
+  const float flo = (float)lo, fhi = (float)hi;
+  if (lo <= hi) {
+#pragma unroll
+    for (int i = 0; i < NF; ++i) ok = ok && fmaf(A[i], i < NL ? flo : fhi, c[i]) > m[i];
+  }
+  if (NL > 0 && lo - 1 >= xl) {
+    bool out = false;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) out = out || fmaf(A[i], flo - 1.0f, c[i]) < -m[i];
+    ok = ok && out;
+  }
+  if (NH > 0 && hi + 1 <= xh) {
+    bool out = false;
+#pragma unroll
+    for (int i = NL; i < NF; ++i) out = out || fmaf(A[i], fhi + 1.0f, c[i]) < -m[i];
+    ok = ok && out;
+  }
+  if (zout) {
+    lo = xl;
+    hi = xl - 1;
+    ok = true;
+  }
+  careful = !ok;
+}
+
 // Black decision of one sample where the FP32 cell cannot decide it: FP64
 // mapped coordinate (definition), its support, and the plain partner image.
 static __device__ __noinline__ bool black_exact(const ItemRec& r, const DevProblem& pr, int x, int y, int z) {
@@ -321,6 +417,7 @@ struct WarpSmem {
   ItemRec rec;
   int2 meta[32];     // (exclusive voxel prefix, own plain index of x0) per row
   float4 pr0[32];    // mapped partner-relative coordinate of x0 per row
+  int forder, fshape;  // fast pass: the item's faces sorted by the sign of A.x (face_order)
 };
 
 template <int ST>
@@ -494,6 +591,10 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
       const int Ox = r.O[0], Oy = r.O[1], Oz = r.O[2];
       const int xl = r.b0[0] - Ox, xh = r.b1[0] - Ox;
       const int by0 = r.b0[1], by1 = r.b1[1];
+      if constexpr (FAST) {
+        if (lane == 0) face_order(r, ws->forder, ws->fshape);
+        __syncwarp();
+      }
       for (int zb = r.b0[2]; zb <= r.b1[2]; zb += 32) {
         const int z = zb + lane;
         int ycnt = 0, ylo = 0;
@@ -530,7 +631,21 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           bool careful = false;
           if (has_row) {
             int lo, hi;
-            row_span<FAST>(r, fp, xl, xh, yrow - Oy, zrow - Oz, lo, hi, careful);
+            const int yi = yrow - Oy, zi = zrow - Oz;
+            if constexpr (FAST) {
+              const int forder = *(volatile int*)&ws->forder;
+              switch (*(volatile int*)&ws->fshape) {
+                case 0x13: row_span_sorted<3, 1>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
+                case 0x22: row_span_sorted<2, 2>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
+                case 0x31: row_span_sorted<1, 3>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
+                case 0x12: row_span_sorted<2, 1>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
+                case 0x21: row_span_sorted<1, 2>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
+                case 0x11: row_span_sorted<1, 1>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
+                default: row_span<true>(r, fp, xl, xh, yi, zi, lo, hi, careful);
+              }
+            } else {
+              row_span<false>(r, fp, xl, xh, yi, zi, lo, hi, careful);
+            }
             if (hi >= lo) {
               xcnt = hi - lo + 1;
               x0 = lo + Ox;
