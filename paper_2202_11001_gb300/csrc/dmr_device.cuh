@@ -515,9 +515,13 @@ static __device__ __forceinline__ int black_near(unsigned long long zm, float fx
 
 // Cell flags (built with the corner cells): bit0 some corner is 0, bit1 all
 // corners are 0, bit2 every voxel of the 4x4x4 block around the cell is 0,
-// bit3 no voxel of that block is 0.  The exact support of a sample always
-// lies inside that block, so bits 2/3 settle the black test outright.
-enum { CF_ANY0 = 1, CF_ALL0 = 2, CF_NB_ALL0 = 4, CF_NB_NONE0 = 8 };
+// bit3 no voxel of that block is 0, bit4 = bit0 and neither bit2 nor bit3.
+// The exact support of a sample always lies inside that block, so bits 2/3
+// settle the black test outright (bit2 implies bit1, bit3 rules out bit1);
+// a cell with no 0 corner is never black (every support shares a corner
+// with the FP32 cell).  So the test is bit1, except where bit4 is set and
+// the sample lies near a cell face.
+enum { CF_ANY0 = 1, CF_ALL0 = 2, CF_NB_ALL0 = 4, CF_NB_NONE0 = 8, CF_NEAR = 16 };
 
 // Threads per SM the register budget is sized for (2048 / 1024 / 768 / 512).
 #ifndef DMR_RASTER_THREADS_PER_SM
@@ -741,17 +745,11 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
                 float d2 = dd * dd;
                 if (black) {
                   const unsigned f = cf[u];
-                  bool blk;
-                  if (f & (CF_NB_ALL0 | CF_NB_NONE0)) {
-                    blk = (f & CF_NB_ALL0) != 0;
-                  } else if (!(f & CF_ANY0)) {
-                    blk = false;
-                  } else {
+                  bool blk = (f & CF_ALL0) != 0;
+                  if (f & CF_NEAR) {
                     const bool nearp = fminf(fminf(fx[u], fy[u]), fz[u]) <= delta ||
                                        fmaxf(fmaxf(fx[u], fy[u]), fz[u]) >= 1.0f - delta;
-                    if (!nearp) {
-                      blk = (f & CF_ALL0) != 0;
-                    } else {
+                    if (nearp) {
                       const int dec = black_near(__ldg(cmask + cix[u]), fx[u], fy[u], fz[u], delta);
                       if (dec >= 0) {
                         blk = dec != 0;

@@ -96,7 +96,10 @@ __global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz,
     w.w = raw[6] | (raw[7] << 16);
     ((uint4*)cells)[id] = w;
   }
-  cflag[id] = (uint8_t)(any0 | (all0 << 1) | (nb_all0 << 2) | (nb_none0 << 3));
+  // bit 4: the cell holds a 0 corner but its block is neither all 0 nor free
+  // of 0s, so a sample near a cell face may need more than the corner flags
+  const int near = any0 && !nb_all0 && !nb_none0;
+  cflag[id] = (uint8_t)(any0 | (all0 << 1) | (nb_all0 << 2) | (nb_none0 << 3) | (near << 4));
 }
 
 void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag,
