@@ -180,6 +180,7 @@ struct dmr_problem {
   void* cells[2] = {nullptr, nullptr};
   uint8_t* cflag[2] = {nullptr, nullptr};
   unsigned long long* cmask[2] = {nullptr, nullptr};
+  int* nzsat[2] = {nullptr, nullptr};
   int4* d_tet = nullptr;
   uint32_t* d_fperm = nullptr;
   uint8_t* d_fix = nullptr;
@@ -349,6 +350,7 @@ void release_problem(dmr_problem* p) {
     dfree(p->cells[k]);
     dfree(p->cflag[k]);
     dfree(p->cmask[k]);
+    dfree(p->nzsat[k]);
   }
   dfree(p->d_tet); dfree(p->d_fperm); dfree(p->d_fix); dfree(p->d_restvol); dfree(p->d_guide);
   dfree(p->d_star_ptr); dfree(p->d_star);
@@ -473,6 +475,14 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
     }
     launch_convert_image(src, d->img_dtype, p->plain[k], p->storage, nv, p->st);
     launch_build_cells(p->plain[k], p->storage, p->n[k], p->cells[k], p->cflag[k], p->cmask[k], p->st);
+    {
+      // nonzero counts fit an int below 2^31 voxels; larger images go without
+      const long ns = (long)(p->n[k][0] + 1) * (p->n[k][1] + 1) * (p->n[k][2] + 1);
+      if (nv < (1L << 31)) {
+        if ((rc = dalloc(&p->nzsat[k], ns))) goto fail_;
+        launch_build_nzsat(p->plain[k], p->storage, p->n[k], p->nzsat[k], p->st);
+      }
+    }
     if (tmp) {
       cudaStreamSynchronize(p->st);
       cudaFree(tmp);
@@ -554,6 +564,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       h.cells[k] = p->cells[k];
       h.cflag[k] = p->cflag[k];
       h.cmask[k] = p->cmask[k];
+      h.nzsat[k] = p->nzsat[k];
       for (int a = 0; a < 3; ++a) {
         h.n[k][a] = p->n[k][a];
         h.spd[k][a] = p->sp[k][a];

@@ -592,6 +592,9 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
       const int nxo = pr.n[d][0], nyo = pr.n[d][1];
       const unsigned Sy = (unsigned)(pr.n[1 - d][0] + 2), Sz = (unsigned)(pr.n[1 - d][1] + 2) * Sy;
       const bool black = pr.black_rule != 0;
+      const bool pzero = (r.flags & 4) != 0;
+      // cell flags are read only where a sample may be black
+      const bool cfload = black && !(r.flags & 8);
       const int Ox = r.O[0], Oy = r.O[1], Oz = r.O[2];
       const int xl = r.b0[0] - Ox, xh = r.b1[0] - Ox;
       const int by0 = r.b0[1], by1 = r.b1[1];
@@ -685,6 +688,29 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           // samples per lane), folded into the Kahan pair afterwards; the
           // fold points do not depend on the tile shape
           float bsum = 0.f;
+          if (pzero) {
+            // every partner voxel these samples can reach is 0: each sample is
+            // 0 and black, so only the own image is read.  Same per-lane order
+            // and fold points as the loop below (identical sums).
+            for (int vb = 0; vb < T; vb += 32) {
+              if (vb != 0 && (vb & 255) == 0) {
+                const float yk = bsum - comp;
+                const float tk = sum + yk;
+                comp = (tk - sum) - yk;
+                sum = tk;
+                bsum = 0.f;
+              }
+              const unsigned bit = (xcnt > 0 && xexcl >= vb && xexcl < vb + 32) ? (1u << (xexcl - vb)) : 0u;
+              const unsigned sm = __reduce_or_sync(FULL_MASK, bit);
+              const int row = rows_before + __popc(sm & lemask) - 1;
+              rows_before += __popc(sm);
+              if (vb + lane < T) {
+                const int2 mt = ws->meta[row];
+                const float o = load_plain<ST>(own_img, mt.y + (vb + lane - mt.x));
+                bsum += black ? (o != 0.0f ? 1.0f : 0.0f) : o * o;
+              }
+            }
+          } else
           for (int vb = 0; vb < T; vb += 32 * VPL) {
             if (vb != 0 && (vb & 255) == 0) {
               const float yk = bsum - comp;
@@ -732,7 +758,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
                 oi[u] = mt.y + dx;
                 cell_load<ST>(cells, ci, cell[u]);
                 own[u] = load_plain<ST>(own_img, oi[u]);
-                cf[u] = black ? __ldg(cflag + ci) : (uint8_t)0;
+                cf[u] = cfload ? __ldg(cflag + ci) : (uint8_t)0;
               }
             }
             // stage B: interpolate, compare, accumulate

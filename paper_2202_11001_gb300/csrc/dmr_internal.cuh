@@ -28,6 +28,9 @@ struct DevProblem {
   // per cell: bit (dz+1)*16 + (dy+1)*4 + (dx+1) set when voxel (i+dx, j+dy,
   // k+dz) (clamped) is 0, for dx, dy, dz in -1..2
   const unsigned long long* cmask[2];
+  // per image: count of nonzero voxels in [0, x) x [0, y) x [0, z), array
+  // [(nz+1)][(ny+1)][(nx+1)] (NULL for images of 2^31 voxels or more)
+  const int* nzsat[2];
   int n[2][3];
   double spd[2][3];
   float sp[2][3];
@@ -70,7 +73,8 @@ struct DevProblem {
 // "partner" = the other mesh.  Relative coordinates are taken against the
 // integer origins O (own) and Op (partner).
 struct __align__(16) ItemRec {
-  int flags;        // bit0: rasterise (6V_own > 0)
+  int flags;        // bit0: rasterise (6V_own > 0); bit1: clamp-free map; bit2 / bit3: every
+                    // partner voxel a sample of this item can reach is 0 / is not 0
   int prob;
   int tet;
   int dir;
@@ -130,6 +134,9 @@ struct Batch {
 void launch_convert_image(const void* src, int src_dtype, void* dst, int dst_dtype, long n, cudaStream_t st);
 void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag,
                         unsigned long long* cmask, cudaStream_t st);
+// Summed nonzero counts of an image (DevProblem::nzsat); sat holds
+// (nx+1)(ny+1)(nz+1) ints.
+void launch_build_nzsat(const void* plain, int dtype, const int n[3], int* sat, cudaStream_t st);
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
 void launch_refine(const double* coarse, int n_cand, const int m[3], double* fine, cudaStream_t st);
 void launch_link_check(const DevProblem* probs, const DevProblem& hp, const int* cands, int n_cand, int* out,

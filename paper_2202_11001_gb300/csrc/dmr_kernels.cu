@@ -102,6 +102,65 @@ __global__ void k_build_cells(const void* plain, int st, int nx, int ny, int nz,
   cflag[id] = (uint8_t)(any0 | (all0 << 1) | (nb_all0 << 2) | (nb_none0 << 3) | (near << 4));
 }
 
+// Summed-volume table of nonzero voxels: S[z][y][x] = number of nonzero
+// voxels with coordinates below (x, y, z) on every axis.  Initialised with the
+// indicator shifted by one, then prefix-summed along x, y and z (one thread
+// per line).
+__global__ void k_nzsat_init(const void* plain, int st, int nx, int ny, int nz, int* S) {
+  const long X = nx + 1, Y = ny + 1, Z = nz + 1;
+  const long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (id >= X * Y * Z) return;
+  const int x = (int)(id % X), y = (int)((id / X) % Y), z = (int)(id / (X * Y));
+  int v = 0;
+  if (x > 0 && y > 0 && z > 0) v = load_plain_dyn(plain, st, ((long)(z - 1) * ny + (y - 1)) * nx + (x - 1)) != 0.0f;
+  S[id] = v;
+}
+
+__global__ void k_nzsat_scan(int* S, int X, int Y, int Z, int axis) {
+  const long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long base, stride;
+  int len;
+  if (axis == 0) {
+    if (id >= (long)Y * Z) return;
+    base = id * X;
+    stride = 1;
+    len = X;
+  } else if (axis == 1) {
+    if (id >= (long)X * Z) return;
+    base = (id / X) * X * Y + id % X;
+    stride = X;
+    len = Y;
+  } else {
+    if (id >= (long)X * Y) return;
+    base = id;
+    stride = (long)X * Y;
+    len = Z;
+  }
+  int acc = 0;
+  for (int i = 0; i < len; ++i) {
+    acc += S[base + i * stride];
+    S[base + i * stride] = acc;
+  }
+}
+
+void launch_build_nzsat(const void* plain, int dtype, const int n[3], int* sat, cudaStream_t st) {
+  const int X = n[0] + 1, Y = n[1] + 1, Z = n[2] + 1;
+  const long N = (long)X * Y * Z;
+  k_nzsat_init<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(plain, dtype, n[0], n[1], n[2], sat);
+  const long lines[3] = {(long)Y * Z, (long)X * Z, (long)X * Y};
+  for (int a = 0; a < 3; ++a)
+    k_nzsat_scan<<<(unsigned)((lines[a] + 127) / 128), 128, 0, st>>>(sat, X, Y, Z, a);
+}
+
+// Nonzero voxels in the box [q0, q1] (inclusive, inside the image).
+static __device__ __forceinline__ long nz_in_box(const int* S, const int* n, const int q0[3], const int q1[3]) {
+  const long X = n[0] + 1, XY = X * (n[1] + 1);
+  auto at = [&](int x, int y, int z) { return (long)__ldg(S + z * XY + y * X + x); };
+  const int x0 = q0[0], y0 = q0[1], z0 = q0[2], x1 = q1[0] + 1, y1 = q1[1] + 1, z1 = q1[2] + 1;
+  return at(x1, y1, z1) - at(x0, y1, z1) - at(x1, y0, z1) - at(x1, y1, z0) + at(x0, y0, z1) + at(x0, y1, z0) +
+         at(x1, y0, z0) - at(x0, y0, z0);
+}
+
 void launch_build_cells(const void* plain, int dtype, const int n[3], void* cells, uint8_t* cflag,
                         unsigned long long* cmask, cudaStream_t st) {
   long N = (long)(n[0] + 2) * (n[1] + 2) * (n[2] + 2);
@@ -405,12 +464,30 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
     // coordinate of this tet can leave [-1, n].  fminf/fmaxf skip NaN, so
     // finiteness is checked explicitly: a NaN partner vertex or map entry
     // takes the clamped path.
+    bool mapok = M < 4096.0f && pfin;
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < 4; ++j) mapok = mapok && isfinite(R.G[c][j]);
     {
-      bool in = M < 4096.0f && pfin;
+      bool in = mapok;
       for (int a = 0; a < 3; ++a) in = in && plo[a] >= -0.75f && phi[a] <= (float)np[a] - 0.25f;
-      for (int c = 0; c < 3; ++c)
-        for (int j = 0; j < 4; ++j) in = in && isfinite(R.G[c][j]);
       if (in) R.flags |= 2;
+    }
+    // bit2: no nonzero partner voxel within 2 voxels of the partner tet's box
+    // (clamped to the image).  A voxel inside the own tet maps into the
+    // partner tet (the FP32 map within a small fraction of a voxel of it, as
+    // for bit1), so its FP32 cell and its exact support, clamped, lie in that
+    // region: the sample is then 0 and black.
+    if (mapok && pr.nzsat[1 - d]) {
+      int q0[3], q1[3];
+      for (int a = 0; a < 3; ++a) {
+        const float hiv = (float)(np[a] - 1);
+        q0[a] = (int)fminf(fmaxf(floorf(plo[a]) - 2.0f, 0.0f), hiv);
+        q1[a] = (int)fminf(fmaxf(ceilf(phi[a]) + 2.0f, 0.0f), hiv);
+      }
+      const long nzc = nz_in_box(pr.nzsat[1 - d], np, q0, q1);
+      const long vol = (long)(q1[0] - q0[0] + 1) * (q1[1] - q0[1] + 1) * (q1[2] - q0[2] + 1);
+      if (nzc == 0) R.flags |= 4;
+      if (nzc == vol) R.flags |= 8;  // no 0 there: no sample is black
     }
     R.gx[0] = 1.0f + R.G[0][0];
     R.gx[1] = R.G[1][0];

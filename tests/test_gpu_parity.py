@@ -105,6 +105,17 @@ def test_ellipsoid64_full_and_partial_black_rule():
     assert_obj_close(g.eval_partial(gids, cids, tc), o.eval_partial(groups, gids, cids, tc), what="trial objectives")
 
 
+def test_ellipsoid64_black_rule_off():
+    """The same ellipsoids with the black rule off: tets whose partner region
+    is all background (every reachable partner voxel 0) contribute the own
+    image's squares; per-tet terms and objectives against the oracle."""
+    pr = synth.ellipsoid_pair(seed=2, C=4)
+    g, o = make_pair(pr, model=orc.LINEAR, black=False)
+    assert_obj_close(g.eval_full(pr["coords"]), o.eval_full(pr["coords"]))
+    for c in range(4):
+        assert_terms_match(g, o, c)
+
+
 def test_plan_generation_matches_sequential_and_oracle():
     """The CUDA-graph generation plan (propose, partial evaluation,
     accept-if-improves, commit for every wave) equals the same steps through
