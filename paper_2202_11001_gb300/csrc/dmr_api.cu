@@ -1459,7 +1459,7 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
     cudaEventRecordWithFlags(pl->ev[3 * w + 2], cs, cudaEventRecordExternal);
     launches += 2 + kRasterLaunches;
     if (any_ng) {
-      // the fork is recorded inside launch_raster after the fast kernel
+      // the fork is recorded inside launch_raster before the fast kernel
       launch_landmarks_partial(d_probs, b, cs2);
       cudaEventRecord(ev_join, cs2);
       cudaStreamWaitEvent(cs, ev_join, 0);

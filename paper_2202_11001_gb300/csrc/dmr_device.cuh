@@ -879,6 +879,10 @@ static void raster_launch(const DevProblem* probs, const Batch& b, int warps, in
                           cudaStream_t side, cudaEvent_t fork) {
   const int vpl = vpw >= 128 ? 4 : (vpw >= 64 ? 2 : 1);
   bool done = false;
+  if (side && fork) {
+    cudaEventRecord(fork, st);
+    cudaStreamWaitEvent(side, fork, 0);
+  }
 #define DMR_RL(W, V)                                          \
   if (!done && warps == W && vpl == V) {                      \
     raster_launch_one<ST, W, V, true>(probs, b, n_sm, st);    \
@@ -889,10 +893,6 @@ static void raster_launch(const DevProblem* probs, const Batch& b, int warps, in
   DMR_RL(16, 1) DMR_RL(16, 2) DMR_RL(16, 4)
 #undef DMR_RL
   if (!done) raster_launch_one<ST, 4, 1, true>(probs, b, n_sm, st);
-  if (side && fork) {
-    cudaEventRecord(fork, st);
-    cudaStreamWaitEvent(side, fork, 0);
-  }
   raster_launch_one<ST, 4, 1, false>(probs, b, n_sm, st);
 }
 

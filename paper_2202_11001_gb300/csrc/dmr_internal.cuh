@@ -144,9 +144,10 @@ void launch_link_check(const DevProblem* probs, const DevProblem& hp, const int*
 void launch_gather_deltas(const double* const* raw, const int* slot_q, const long long* slot_src, const int* raw_G,
                           int n_slots, int G, double* out, cudaStream_t st);
 // Raster kernels: fast pass, then the full-logic pass over the items it
-// handed over.  With a side stream, `fork` is recorded on `st` after the fast
-// pass and the side stream waits on it (work placed there runs beside the
-// full-logic pass).
+// handed over.  With a side stream, `fork` is recorded on `st` before the
+// fast pass and the side stream waits on it: work placed there (the guidance
+// points) fills the SM slots the persistent fast pass leaves free, mostly in
+// its tail and beside the full-logic pass.
 void launch_raster(const DevProblem* probs, const Batch& b, int storage_dtype, int warps, int vpw, int n_sm,
                    cudaStream_t st, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr);
 void launch_raster_f32(const DevProblem* probs, const Batch& b, int warps, int vpw, int n_sm, cudaStream_t st,

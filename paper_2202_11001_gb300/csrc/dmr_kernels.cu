@@ -186,7 +186,7 @@ __device__ __forceinline__ double pick4d(const double (&v)[4][3], int i, int a) 
 
 // One thread per (trial, tet): fold count, deformation, and the two
 // direction records (Sec. 2.3.1-2.3.4).
-__global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b) {
+__global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch b) {
   int tt = blockIdx.x * blockDim.x + threadIdx.x;
   if (tt == 0 && b.work) b.work[0] = b.work[1] = b.work[2] = 0u;
   if (tt >= b.n_tt) return;
@@ -305,6 +305,30 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
         mhi[mesh][a] = fmaxf(mhi[mesh][a], v);
         mfin[mesh] = mfin[mesh] && isfinite(v);
       }
+    }
+  }
+
+  // Zero-region bits of each direction (ItemRec::flags bit2 / bit3, kept
+  // below only where the map is finite and small): no nonzero / no zero
+  // partner voxel within 2 voxels of the partner tet's box (clamped to the
+  // image).  A voxel inside the own tet maps into the partner tet (the FP32
+  // map within a small fraction of a voxel of it, as for bit1), so its FP32
+  // cell and its exact support, clamped, lie in that region: with no nonzero
+  // voxel there the sample is 0 and black, with no 0 it is not black.
+  int zbits[2] = {0, 0};
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const int* np = pr.n[1 - d];
+    if (mfin[1 - d] && pr.nzsat[1 - d]) {
+      int q0[3], q1[3];
+      for (int a = 0; a < 3; ++a) {
+        const float hiv = (float)(np[a] - 1);
+        q0[a] = (int)fminf(fmaxf(floorf(mlo[1 - d][a]) - 2.0f, 0.0f), hiv);
+        q1[a] = (int)fminf(fmaxf(ceilf(mhi[1 - d][a]) + 2.0f, 0.0f), hiv);
+      }
+      const long nzc = nz_in_box(pr.nzsat[1 - d], np, q0, q1);
+      const long vol = (long)(q1[0] - q0[0] + 1) * (q1[1] - q0[1] + 1) * (q1[2] - q0[2] + 1);
+      zbits[d] = (nzc == 0 ? 4 : 0) | (nzc == vol ? 8 : 0);
     }
   }
 
@@ -472,23 +496,7 @@ __global__ void __launch_bounds__(128) k_setup(const DevProblem* probs, Batch b)
       for (int a = 0; a < 3; ++a) in = in && plo[a] >= -0.75f && phi[a] <= (float)np[a] - 0.25f;
       if (in) R.flags |= 2;
     }
-    // bit2: no nonzero partner voxel within 2 voxels of the partner tet's box
-    // (clamped to the image).  A voxel inside the own tet maps into the
-    // partner tet (the FP32 map within a small fraction of a voxel of it, as
-    // for bit1), so its FP32 cell and its exact support, clamped, lie in that
-    // region: the sample is then 0 and black.
-    if (mapok && pr.nzsat[1 - d]) {
-      int q0[3], q1[3];
-      for (int a = 0; a < 3; ++a) {
-        const float hiv = (float)(np[a] - 1);
-        q0[a] = (int)fminf(fmaxf(floorf(plo[a]) - 2.0f, 0.0f), hiv);
-        q1[a] = (int)fminf(fmaxf(ceilf(phi[a]) + 2.0f, 0.0f), hiv);
-      }
-      const long nzc = nz_in_box(pr.nzsat[1 - d], np, q0, q1);
-      const long vol = (long)(q1[0] - q0[0] + 1) * (q1[1] - q0[1] + 1) * (q1[2] - q0[2] + 1);
-      if (nzc == 0) R.flags |= 4;
-      if (nzc == vol) R.flags |= 8;  // no 0 there: no sample is black
-    }
+    if (mapok) R.flags |= zbits[d];
     R.gx[0] = 1.0f + R.G[0][0];
     R.gx[1] = R.G[1][0];
     R.gx[2] = R.G[2][0];
@@ -889,8 +897,17 @@ __device__ __forceinline__ bool sorted_has(const int* tl, int n, int v) {
   return false;
 }
 
+// Partial evaluation, guidance points (Sec. 2.3.3): one warp per trial.  The
+// points whose cached tet the trial touches (or that are unlocated) are taken
+// 32 at a time in index order: the lanes first test all (point, touched tet)
+// pairs (the lowest tet index that contains a point wins, as a scan in order
+// would find), then evaluate the points' terms side by side; the changes are
+// added on one lane in index order.
 __global__ void __launch_bounds__(32 * kLmWarps, 3) k_landmarks_partial(const DevProblem* probs, Batch b) {
   __shared__ int s_tl[kLmWarps][kLmTl];
+  __shared__ int s_found[kLmWarps][32];
+  __shared__ double s_dg[kLmWarps][32];
+  const int w = threadIdx.x >> 5;
   int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (k >= b.n_trials) return;
@@ -899,7 +916,7 @@ __global__ void __launch_bounds__(32 * kLmWarps, 3) k_landmarks_partial(const De
   const int cand = b.tr_cand[k];
   const int first = b.tr_first[k], ntt = b.tr_ntt[k];
   const int* tl = b.tt_tet + first;
-  int* stl = s_tl[threadIdx.x >> 5];
+  int* stl = s_tl[w];
   const bool staged = ntt <= kLmTl;
   if (staged)
     for (int j = lane; j < ntt; j += 32) stl[j] = tl[j];
@@ -909,51 +926,57 @@ __global__ void __launch_bounds__(32 * kLmWarps, 3) k_landmarks_partial(const De
   double gd = 0.0;
   int ud = 0;
   for (int base = 0; base < 2 * ng; base += 32) {
-    int e = base + lane;
+    const int e = base + lane;
     bool aff = false;
     int told = -2;
     if (e < 2 * ng) {
-      int mesh = e / ng, i = e % ng;
+      const int mesh = e / ng, i = e % ng;
       told = pr.c_loc[((size_t)cand * 2 + mesh) * ng + i];
       aff = told < 0 || sorted_has(sl, ntt, told);
     }
-    unsigned am = __ballot_sync(FULL_MASK, aff);
-    while (am) {
-      int src = __ffs(am) - 1;
-      am &= am - 1;
-      int ee = base + src;
-      int mesh = ee / ng, i = ee % ng;
-      int t_old = __shfl_sync(FULL_MASK, told, src);
-      double p[3];
-      for (int a = 0; a < 3; ++a) p[a] = pr.guide[6 * i + 3 * mesh + a];
-      float pmag = fmaxf(fabsf((float)p[0]), fmaxf(fabsf((float)p[1]), fabsf((float)p[2])));
-      int found = -1;
-      for (int jb = 0; jb < ntt && found < 0; jb += 32) {
-        int j = jb + lane;
-        bool in = false;
-        if (j < ntt) {
-          const ItemRec& r = b.rec[2 * (size_t)(first + j) + mesh];
-          in = lm_test(r, pr.fperm[sl[j]], p, pmag);
-        }
-        unsigned m = __ballot_sync(FULL_MASK, in);
-        if (m) found = jb + __ffs(m) - 1;
-      }
-      if (lane == 0) {
-        double term = found >= 0 ? landmark_term(b.rec[2 * (size_t)(first + found) + mesh], pr, p, mesh, i) : 0.0;
-        size_t li = ((size_t)cand * 2 + mesh) * ng + i;
-        double old = pr.c_gterm[li];
-        gd = dadd(gd, dsub(term, old));
-        ud += (found < 0 ? 1 : 0) - (t_old < 0 ? 1 : 0);
-        if (naff < b.aff_cap) {
-          size_t o = (size_t)k * b.aff_cap + naff;
-          b.aff_idx[o] = ee;
-          b.aff_loc[o] = found >= 0 ? sl[found] : -1;
-          b.aff_term[o] = term;
-        }
-        ++naff;
-      }
+    const unsigned am = __ballot_sync(FULL_MASK, aff);
+    if (!am) continue;
+    const int na = __popc(am);
+    // slot of this lane's point among the affected ones, in index order
+    const int slot = __popc(am & ((1u << lane) - 1u));
+    s_found[w][lane] = INT_MAX;
+    __syncwarp();
+    // (affected point, touched tet) pairs
+    for (int q = lane; q < na * ntt; q += 32) {
+      const int a = q / ntt, j = q - a * ntt;
+      const int src = __fns(am, 0, a + 1);  // lane of the a-th affected point
+      const int ee = base + src;
+      const int mesh = ee / ng, i = ee % ng;
+      double pp[3];
+      for (int c = 0; c < 3; ++c) pp[c] = pr.guide[6 * i + 3 * mesh + c];
+      const float pmag = fmaxf(fabsf((float)pp[0]), fmaxf(fabsf((float)pp[1]), fabsf((float)pp[2])));
+      const ItemRec& r = b.rec[2 * (size_t)(first + j) + mesh];
+      if (lm_test(r, pr.fperm[sl[j]], pp, pmag)) atomicMin(&s_found[w][a], j);
     }
+    __syncwarp();
+    if (aff) {
+      const int mesh = e / ng, i = e % ng;
+      double pp[3];
+      for (int c = 0; c < 3; ++c) pp[c] = pr.guide[6 * i + 3 * mesh + c];
+      const int fj = s_found[w][slot];
+      const int found = fj == INT_MAX ? -1 : fj;
+      const double term = found >= 0 ? landmark_term(b.rec[2 * (size_t)(first + found) + mesh], pr, pp, mesh, i) : 0.0;
+      const size_t li = ((size_t)cand * 2 + mesh) * ng + i;
+      s_dg[w][slot] = dsub(term, pr.c_gterm[li]);
+      if (naff + slot < b.aff_cap) {
+        const size_t o = (size_t)k * b.aff_cap + naff + slot;
+        b.aff_idx[o] = e;
+        b.aff_loc[o] = found >= 0 ? sl[found] : -1;
+        b.aff_term[o] = term;
+      }
+      ud += (found < 0 ? 1 : 0) - (told < 0 ? 1 : 0);
+    }
+    __syncwarp();
+    if (lane == 0)
+      for (int a = 0; a < na; ++a) gd = dadd(gd, s_dg[w][a]);
+    naff += na;
   }
+  ud = __reduce_add_sync(FULL_MASK, ud);
   if (lane == 0) {
     b.aff_n[k] = min(naff, b.aff_cap);
     b.tr_delta[4 * (size_t)k + 2] = gd;
