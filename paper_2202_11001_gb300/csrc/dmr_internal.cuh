@@ -94,7 +94,6 @@ struct __align__(16) ItemRec {
   float chi[4];
   double X[4][3];   // own vertices FP64 (abs)
   double XP[4][3];  // partner vertices FP64 (abs): the exact map is rebuilt from them
-  double Gd[3][3];  // FP64 map matrix (fused multiply-adds, a few ulps from the exact order)
 };
 
 // Kernels one launch_raster call launches (fast, full-logic).

@@ -367,7 +367,6 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     for (int c = 0; c < 3; ++c)
       for (int j = 0; j < 3; ++j) {
         Gd[c][j] = fma(Dm[0][c], rr[0][j], fma(Dm[1][c], rr[1][j], Dm[2][c] * rr[2][j])) * inv;
-        R.Gd[c][j] = Gd[c][j];
       }
     // linear-elastic energy from the source->target map (direction 0)
     if (d == 0 && pr.model == 1 && vol6[0] != 0.0 && isfinite(vol6[0])) {
