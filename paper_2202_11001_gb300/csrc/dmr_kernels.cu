@@ -186,6 +186,12 @@ __device__ __forceinline__ double pick4d(const double (&v)[4][3], int i, int a) 
 
 // One thread per (trial, tet): fold count, deformation, and the two
 // direction records (Sec. 2.3.1-2.3.4).
+// k_setup writes records as 16-byte words; the layout it relies on
+static_assert(offsetof(ItemRec, b0) == 16 && offsetof(ItemRec, b1) == 32 && offsetof(ItemRec, O) == 48 &&
+                  offsetof(ItemRec, Op) == 64 && offsetof(ItemRec, cbase) == 80 && offsetof(ItemRec, vr) % 16 == 0 &&
+                  offsetof(ItemRec, X) % 16 == 0 && offsetof(ItemRec, XP) % 16 == 0 && sizeof(ItemRec) % 16 == 0,
+              "ItemRec layout");
+
 __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch b) {
   int tt = blockIdx.x * blockDim.x + threadIdx.x;
   if (tt == 0 && b.work) b.work[0] = b.work[1] = b.work[2] = 0u;
@@ -332,7 +338,8 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     }
   }
 
-  // the two directions (unrolled so the vertex arrays stay in registers)
+  // the two directions (unrolled so the vertex arrays stay in registers);
+  // each record is assembled in registers and written with 16-byte stores
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
     ItemRec& R = b.rec[2 * (size_t)tt + d];
@@ -342,14 +349,16 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     const int* n = pr.n[d];
     const int* np = pr.n[1 - d];
     int flags = (vol6[d] > 0 && isfinite(vol6[d])) ? 1 : 0;
-    R.prob = pi;
-    R.tet = t;
-    R.dir = d;
-    for (int i = 0; i < 4; ++i)
-      for (int a = 0; a < 3; ++a) {
-        R.X[i][a] = own[i][a];
-        R.XP[i][a] = par[i][a];
+    {
+      double2* xs = reinterpret_cast<double2*>(&R.X[0][0]);
+      double2* xp = reinterpret_cast<double2*>(&R.XP[0][0]);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int i0 = (2 * q) / 3, a0 = (2 * q) % 3, i1 = (2 * q + 1) / 3, a1 = (2 * q + 1) % 3;
+        xs[q] = make_double2(own[i0][a0], own[i1][a1]);
+        xp[q] = make_double2(par[i0][a0], par[i1][a1]);
       }
+    }
     // map G = [D1 D2 D3][r1; r2; r3] / det for the FP32 path, with fused
     // multiply-adds (within a few FP64 ulps of the exact-order map, which
     // the decisions that need it rebuild from X and XP); det = 6V_own
@@ -365,9 +374,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     const double inv = sg / vol6[d];
     double Gd[3][3];
     for (int c = 0; c < 3; ++c)
-      for (int j = 0; j < 3; ++j) {
-        Gd[c][j] = fma(Dm[0][c], rr[0][j], fma(Dm[1][c], rr[1][j], Dm[2][c] * rr[2][j])) * inv;
-      }
+      for (int j = 0; j < 3; ++j) Gd[c][j] = fma(Dm[0][c], rr[0][j], fma(Dm[1][c], rr[1][j], Dm[2][c] * rr[2][j])) * inv;
     // linear-elastic energy from the source->target map (direction 0)
     if (d == 0 && pr.model == 1 && vol6[0] != 0.0 && isfinite(vol6[0])) {
       float H[3][3];
@@ -386,12 +393,11 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
         }
       def = (double)(pr.rest_vol[t] * (pr.mu * ee + 0.5f * pr.lam * tr * tr));
     }
+    int4* R4 = reinterpret_cast<int4*>(&R);  // header, b0, b1, O, Op, cbase
     if (!flags) {
-      R.flags = 0;
-      for (int a = 0; a < 4; ++a) {
-        R.b0[a] = 1;
-        R.b1[a] = 0;
-      }
+      R4[0] = make_int4(0, pi, t, d);
+      R4[1] = make_int4(1, 1, 1, 1);
+      R4[2] = make_int4(0, 0, 0, 0);
       continue;
     }
     // bbox and origins
@@ -400,33 +406,32 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     const float* plo = mlo[1 - d];
     const float* phi = mhi[1 - d];
     const bool pfin = mfin[1 - d];
-    int O[3], Op[3];
+    int O[3], Op[3], B0[3], B1[3];
     int L = 1;
     for (int a = 0; a < 3; ++a) {
       float cl = ceilf(lo[a]), fh = floorf(hi[a]);
-      int b0 = cl < 0.f ? 0 : (int)fminf(cl, (float)n[a]);
-      int b1 = fh > (float)(n[a] - 1) ? n[a] - 1 : (int)fmaxf(fh, -1.0f);
-      R.b0[a] = b0;
-      R.b1[a] = b1;
+      B0[a] = cl < 0.f ? 0 : (int)fminf(cl, (float)n[a]);
+      B1[a] = fh > (float)(n[a] - 1) ? n[a] - 1 : (int)fmaxf(fh, -1.0f);
       O[a] = (int)fmaxf(fminf(floorf(lo[a]), (float)n[a]), -2.0f);
       Op[a] = (int)fmaxf(fminf(floorf(plo[a]), (float)np[a]), -2.0f);
-      R.O[a] = O[a];
-      R.Op[a] = Op[a];
-      L = max(L, b1 - O[a] + 1);
+      L = max(L, B1[a] - O[a] + 1);
     }
-    R.b0[3] = R.b1[3] = R.O[3] = R.Op[3] = 0;
-    if (R.b0[0] > R.b1[0] || R.b0[1] > R.b1[1] || R.b0[2] > R.b1[2]) flags = 0;
-    R.flags = flags;
+    R4[1] = make_int4(B0[0], B0[1], B0[2], 0);
+    R4[2] = make_int4(B1[0], B1[1], B1[2], 0);
+    R4[3] = make_int4(O[0], O[1], O[2], 0);
+    R4[4] = make_int4(Op[0], Op[1], Op[2], 0);
+    if (B0[0] > B1[0] || B0[1] > B1[1] || B0[2] > B1[2]) flags = 0;
     // own vertices relative to O (FP64 difference; FP32 copy for the slices)
     double vd[4][3];
     float V = 0.f;
     for (int i = 0; i < 4; ++i) {
+      float vr[3];
       for (int a = 0; a < 3; ++a) {
         vd[i][a] = dsub(own[i][a], (double)O[a]);
-        R.vr[i][a] = (float)vd[i][a];
-        V = fmaxf(V, fabsf(R.vr[i][a]));
+        vr[a] = (float)vd[i][a];
+        V = fmaxf(V, fabsf(vr[a]));
       }
-      R.vr[i][3] = 0.f;
+      *reinterpret_cast<float4*>(&R.vr[i][0]) = make_float4(vr[0], vr[1], vr[2], 0.f);
     }
     // faces: inward FP64 normals from the adjugate rows of the map (for a
     // tet of positive volume, rr[m-1] is the inward normal, with the length
@@ -456,18 +461,15 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       const float Ax = (float)nx, Ay = (float)ny, Az = (float)nz, Bp = (float)Bd;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
       const float mu = (1.0f / 2097152.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
-      R.fa[f][0] = Ax;
-      R.fa[f][1] = Ay;
-      R.fa[f][2] = Az;
-      R.fa[f][3] = Bp;
-      R.fm[f][0] = mu;
-      R.fm[f][1] = 1.0f / Ax;
-      R.fm[f][2] = (1.0f / 2097152.0f) * an + 1.5e-14f * (UW + an);
-      // bound on |A.x - s n_x| beyond FP32 rounding: the fused and the
-      // oracle-order FP64 normals differ by a few 2^-53 U W
-      R.fm[f][3] = 3.0e-14f * UW + 1e-30f;
+      *reinterpret_cast<float4*>(&R.fa[f][0]) = make_float4(Ax, Ay, Az, Bp);
+      // fm: margin, 1/A.x, margin growth per voxel of |p - O| (landmarks),
+      // and the bound on |A.x - s n_x| beyond FP32 rounding (the fused and
+      // the oracle-order FP64 normals differ by a few 2^-53 U W)
+      *reinterpret_cast<float4*>(&R.fm[f][0]) = make_float4(
+          mu, 1.0f / Ax, (1.0f / 2097152.0f) * an + 1.5e-14f * (UW + an), 3.0e-14f * UW + 1e-30f);
     }
     // FP32 map relative to the origins: p'_rel = vr + G vr + k
+    float G[3][4];
     float gmax = 0.f, kmax = 0.f;
     for (int c = 0; c < 3; ++c) {
       const double oo0 = dsub((double)O[0], own[0][0]), oo1 = dsub((double)O[1], own[0][1]),
@@ -475,11 +477,12 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       const double d0 = dsub(par[0][c], own[0][c]);
       const double kk = ((double)(O[c] - Op[c]) + d0) + fma(Gd[c][0], oo0, fma(Gd[c][1], oo1, Gd[c][2] * oo2));
       for (int j = 0; j < 3; ++j) {
-        R.G[c][j] = (float)Gd[c][j];
-        gmax = fmaxf(gmax, fabsf(R.G[c][j]));
+        G[c][j] = (float)Gd[c][j];
+        gmax = fmaxf(gmax, fabsf(G[c][j]));
       }
-      R.G[c][3] = (float)kk;
-      kmax = fmaxf(kmax, fabsf(R.G[c][3]));
+      G[c][3] = (float)kk;
+      kmax = fmaxf(kmax, fabsf(G[c][3]));
+      *reinterpret_cast<float4*>(&R.G[c][0]) = make_float4(G[c][0], G[c][1], G[c][2], G[c][3]);
     }
     float M = (float)L * (1.0f + 3.0f * gmax) + kmax + 2.0f;
     // bit1: the partner tet lies within [-0.75, n - 0.25] on every axis and
@@ -489,27 +492,25 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     // takes the clamped path.
     bool mapok = M < 4096.0f && pfin;
     for (int c = 0; c < 3; ++c)
-      for (int j = 0; j < 4; ++j) mapok = mapok && isfinite(R.G[c][j]);
+      for (int j = 0; j < 4; ++j) mapok = mapok && isfinite(G[c][j]);
     {
       bool in = mapok;
       for (int a = 0; a < 3; ++a) in = in && plo[a] >= -0.75f && phi[a] <= (float)np[a] - 0.25f;
-      if (in) R.flags |= 2;
+      if (flags && in) flags |= 2;
     }
-    if (mapok) R.flags |= zbits[d];
-    R.gx[0] = 1.0f + R.G[0][0];
-    R.gx[1] = R.G[1][0];
-    R.gx[2] = R.G[2][0];
-    R.gx[3] = M * (1.0f / 524288.0f);  // black-decision margin delta (2^-19 M)
-    for (int a = 0; a < 3; ++a) {
-      R.clo[a] = (float)(-1 - Op[a]);
-      R.chi[a] = (float)(np[a] - Op[a]);
-    }
-    R.clo[3] = R.chi[3] = 0.f;
+    if (flags && mapok) flags |= zbits[d];
+    R4[0] = make_int4(flags, pi, t, d);
+    // gx: (1 + G00, G10, G20, black-decision margin delta = 2^-19 M)
+    *reinterpret_cast<float4*>(&R.gx[0]) = make_float4(1.0f + G[0][0], G[1][0], G[2][0], M * (1.0f / 524288.0f));
+    *reinterpret_cast<float4*>(&R.clo[0]) =
+        make_float4((float)(-1 - Op[0]), (float)(-1 - Op[1]), (float)(-1 - Op[2]), 0.f);
+    *reinterpret_cast<float4*>(&R.chi[0]) =
+        make_float4((float)(np[0] - Op[0]), (float)(np[1] - Op[1]), (float)(np[2] - Op[2]), 0.f);
     // corner-cell index: cell (i,j,k) with i = Op.x + floor(p'_rel.x) etc.
     unsigned Sy = (unsigned)(np[0] + 2), Sz = (unsigned)((np[1] + 2) * (np[0] + 2));
     unsigned base = ((unsigned)(Op[2] + 1) * (unsigned)(np[1] + 2) + (unsigned)(Op[1] + 1)) * Sy + (unsigned)(Op[0] + 1);
     base -= (unsigned)MAGIC_BITS * (Sz + Sy + 1u);
-    R.cbase = base;
+    R4[5] = make_int4((int)base, 0, 0, 0);
   }
   b.o_def[tt] = def;
 }
