@@ -1465,11 +1465,9 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
       cudaStreamWaitEvent(cs, ev_join, 0);
       ++launches;
     }
-    launch_reduce_partial(d_probs, b, cs);
-    launch_accept(d_probs, b, pl->sc.accept, cs);
-    launch_commit(d_probs, b, pl->sc.accept, trg, d_gptr, d_gpts, pl->cand_ptr + w_c0[w],
-                  pl->cand_trials + w_tr0[w], w_nlist[w], cs);
-    launches += 5;
+    launch_reduce_commit(d_probs, b, pl->sc.accept, trg, d_gptr, d_gpts, pl->cand_ptr + w_c0[w],
+                         pl->cand_trials + w_tr0[w], w_nlist[w], cs);
+    launches += 2;
     e = cudaGetLastError();
   }
   cudaGraph_t g = nullptr;

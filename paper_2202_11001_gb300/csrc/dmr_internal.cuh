@@ -164,6 +164,11 @@ void launch_accept(const DevProblem* probs, const Batch& b, uint8_t* accept, cud
 void launch_commit(const DevProblem* probs, const Batch& b, const uint8_t* accept, const int* tr_group,
                    const int* g_ptr, const int* g_pts, const int* cand_ptr, const int* cand_trials, int n_list,
                    cudaStream_t st);
+// Plans: reduce + accept + per-trial commit fused, then the per-candidate sums
+// (two launches instead of five).
+void launch_reduce_commit(const DevProblem* probs, const Batch& b, uint8_t* accept, const int* tr_group,
+                          const int* g_ptr, const int* g_pts, const int* cand_ptr, const int* cand_trials, int n_list,
+                          cudaStream_t st);
 void launch_propose(const DevProblem* probs, const Batch& b, const int* tr_group, const int* g_ptr, const int* g_pts,
                     const double* deltas, cudaStream_t st);
 

@@ -998,11 +998,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-__global__ void k_reduce_partial(const DevProblem* probs, Batch b, int has_landmarks) {
-  int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (k >= b.n_trials) return;
-  const DevProblem& pr = probs[b.tr_prob ? b.tr_prob[k] : 0];
+// Trial k's deltas and objectives (one warp; lane 0 writes tr_delta and
+// tr_obj); returns the trial's sample count on every lane.
+__device__ __forceinline__ unsigned reduce_trial(const DevProblem& pr, const Batch& b, int k, int lane,
+                                                 int has_landmarks) {
   const int cand = b.tr_cand[k];
   const int first = b.tr_first[k], ntt = b.tr_ntt[k];
   double old[3] = {0, 0, 0}, nw[3] = {0, 0, 0};
@@ -1023,21 +1022,31 @@ __global__ void k_reduce_partial(const DevProblem* probs, Batch b, int has_landm
     nw[q] = warp_sum_d(nw[q]);
   }
   cov = __reduce_add_sync(FULL_MASK, cov);
-  if (lane != 0) return;
-  double* dl = b.tr_delta + 4 * (size_t)k;
-  dl[0] = dsub(nw[0], old[0]);
-  dl[1] = dsub(nw[1], old[1]);
-  double gd = has_landmarks ? dl[2] : 0.0;
-  double ud = has_landmarks ? dl[3] : 0.0;
-  if (!has_landmarks) dl[2] = 0.0;
-  dl[3] = dadd(dsub(nw[2], old[2]), ud);
-  const double* s = pr.sums + 4 * (size_t)cand;
-  double* ob = b.tr_obj + 4 * (size_t)k;
-  ob[0] = dadd(s[0], dl[0]) / pr.sim_norm;
-  ob[1] = dadd(s[1], dl[1]) / pr.def_norm;
-  ob[2] = pr.ng > 0 ? dadd(s[2], gd) / pr.guid_norm : 0.0;
-  ob[3] = dadd(s[3], dl[3]);
-  atomicAdd(pr.samples, (unsigned long long)cov);
+  if (lane == 0) {
+    double* dl = b.tr_delta + 4 * (size_t)k;
+    dl[0] = dsub(nw[0], old[0]);
+    dl[1] = dsub(nw[1], old[1]);
+    double gd = has_landmarks ? dl[2] : 0.0;
+    double ud = has_landmarks ? dl[3] : 0.0;
+    if (!has_landmarks) dl[2] = 0.0;
+    dl[3] = dadd(dsub(nw[2], old[2]), ud);
+    const double* s = pr.sums + 4 * (size_t)cand;
+    double* ob = b.tr_obj + 4 * (size_t)k;
+    ob[0] = dadd(s[0], dl[0]) / pr.sim_norm;
+    ob[1] = dadd(s[1], dl[1]) / pr.def_norm;
+    ob[2] = pr.ng > 0 ? dadd(s[2], gd) / pr.guid_norm : 0.0;
+    ob[3] = dadd(s[3], dl[3]);
+  }
+  return cov;
+}
+
+__global__ void k_reduce_partial(const DevProblem* probs, Batch b, int has_landmarks) {
+  int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (k >= b.n_trials) return;
+  const DevProblem& pr = probs[b.tr_prob ? b.tr_prob[k] : 0];
+  const unsigned cov = reduce_trial(pr, b, k, lane, has_landmarks);
+  if (lane == 0) atomicAdd(pr.samples, (unsigned long long)cov);
 }
 
 void launch_reduce_partial(const DevProblem* probs, const Batch& b, cudaStream_t st) {
@@ -1047,21 +1056,21 @@ void launch_reduce_partial(const DevProblem* probs, const Batch& b, cudaStream_t
 }
 
 // Accept-if-improves (Sec. 2.2), constraint domination first.
+__device__ __forceinline__ bool accept_trial(const DevProblem& pr, const Batch& b, int k) {
+  const double* s = pr.sums + 4 * (size_t)b.tr_cand[k];
+  const double* o = b.tr_obj + 4 * (size_t)k;
+  double cur[4] = {s[0] / pr.sim_norm, s[1] / pr.def_norm, pr.ng > 0 ? s[2] / pr.guid_norm : 0.0, s[3]};
+  if (o[3] != cur[3]) return o[3] < cur[3];
+  bool le = o[0] <= cur[0] && o[1] <= cur[1] && o[2] <= cur[2];
+  bool lt = o[0] < cur[0] || o[1] < cur[1] || o[2] < cur[2];
+  return le && lt;
+}
+
 __global__ void k_accept(const DevProblem* probs, Batch b, uint8_t* accept) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.n_trials) return;
   const DevProblem& pr = probs[b.tr_prob ? b.tr_prob[k] : 0];
-  const double* s = pr.sums + 4 * (size_t)b.tr_cand[k];
-  const double* o = b.tr_obj + 4 * (size_t)k;
-  double cur[4] = {s[0] / pr.sim_norm, s[1] / pr.def_norm, pr.ng > 0 ? s[2] / pr.guid_norm : 0.0, s[3]};
-  bool acc;
-  if (o[3] != cur[3]) acc = o[3] < cur[3];
-  else {
-    bool le = o[0] <= cur[0] && o[1] <= cur[1] && o[2] <= cur[2];
-    bool lt = o[0] < cur[0] || o[1] < cur[1] || o[2] < cur[2];
-    acc = le && lt;
-  }
-  accept[k] = acc ? 1 : 0;
+  accept[k] = accept_trial(pr, b, k) ? 1 : 0;
 }
 
 void launch_accept(const DevProblem* probs, const Batch& b, uint8_t* accept, cudaStream_t st) {
@@ -1137,6 +1146,91 @@ __global__ void k_commit_sums(const DevProblem* probs, Batch b, const uint8_t* a
     double* s = pr.sums + 4 * (size_t)b.tr_cand[k0];
     for (int q = 0; q < 4; ++q) s[q] = dadd(s[q], tot[q]);
   }
+}
+
+// Generation plans: reduce, accept and the per-trial part of the commit in
+// one warp per trial.  The trials of a wave touch disjoint tets and move
+// disjoint points, and every accept decision reads the candidate's sums
+// from before the wave (k_commit_sums, launched after, adds the accepted
+// deltas), so committing a trial's tets, coordinates and guidance points
+// right after its decision gives the same state as the separate kernels.
+// Sample counts are added once per block.
+__global__ void __launch_bounds__(256) k_reduce_commit(const DevProblem* probs, Batch b, int has_landmarks,
+                                                       uint8_t* accept, const int* tr_group, const int* g_ptr,
+                                                       const int* g_pts) {
+  __shared__ unsigned long long s_cov[8];
+  __shared__ int s_pi[8];
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int pi = (k < b.n_trials && b.tr_prob) ? b.tr_prob[k] : 0;
+  const DevProblem& pr = probs[pi];
+  unsigned cov = 0;
+  if (k < b.n_trials) {
+    cov = reduce_trial(pr, b, k, lane, has_landmarks);
+    int acc = 0;
+    if (lane == 0) {
+      acc = accept_trial(pr, b, k) ? 1 : 0;
+      accept[k] = (uint8_t)acc;
+    }
+    acc = __shfl_sync(FULL_MASK, acc, 0);
+    if (acc) {
+      const int cand = b.tr_cand[k];
+      const int first = b.tr_first[k], ntt = b.tr_ntt[k];
+      for (int j = lane; j < ntt; j += 32) {
+        const int tt = first + j;
+        const size_t ci = (size_t)cand * pr.ntet + b.tt_tet[tt];
+        pr.c_ssd[2 * ci] = b.o_ssd[2 * (size_t)tt];
+        pr.c_ssd[2 * ci + 1] = b.o_ssd[2 * (size_t)tt + 1];
+        pr.c_cov[2 * ci] = b.o_cov[2 * (size_t)tt];
+        pr.c_cov[2 * ci + 1] = b.o_cov[2 * (size_t)tt + 1];
+        pr.c_def[ci] = b.o_def[tt];
+        pr.c_fold[ci] = b.o_fold[tt];
+      }
+      const int g = tr_group[k];
+      const int np = g_ptr[g + 1] - g_ptr[g];
+      for (int e = lane; e < 6 * np; e += 32) {
+        const int ma = e / np, j = e % np;
+        const int pid = g_pts[g_ptr[g] + j];
+        pr.coords[((size_t)cand * 6 + ma) * pr.P + pid] = b.tr_coords[(size_t)k * 6 * b.gmax + (size_t)ma * b.gmax + j];
+      }
+      if (b.aff_n) {
+        const int na = b.aff_n[k];
+        for (int e = lane; e < na; e += 32) {
+          const size_t o = (size_t)k * b.aff_cap + e;
+          const size_t li = (size_t)cand * 2 * pr.ng + b.aff_idx[o];
+          pr.c_loc[li] = b.aff_loc[o];
+          pr.c_gterm[li] = b.aff_term[o];
+        }
+      }
+    }
+  }
+  if (lane == 0) {
+    s_cov[w] = cov;
+    s_pi[w] = pi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // one atomic per run of warps of the same problem
+    unsigned long long t = 0;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int i = 0; i < nw; ++i) {
+      t += s_cov[i];
+      if (i + 1 == nw || s_pi[i + 1] != s_pi[i]) {
+        if (t) atomicAdd(probs[s_pi[i]].samples, t);
+        t = 0;
+      }
+    }
+  }
+}
+
+void launch_reduce_commit(const DevProblem* probs, const Batch& b, uint8_t* accept, const int* tr_group,
+                          const int* g_ptr, const int* g_pts, const int* cand_ptr, const int* cand_trials, int n_list,
+                          cudaStream_t st) {
+  if (b.n_trials <= 0) return;
+  const long threads = 32L * b.n_trials;
+  k_reduce_commit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(probs, b, b.aff_n != nullptr, accept, tr_group,
+                                                                      g_ptr, g_pts);
+  k_commit_sums<<<(unsigned)((32L * n_list + 255) / 256), 256, 0, st>>>(probs, b, accept, cand_ptr, cand_trials, n_list);
 }
 
 void launch_commit(const DevProblem* probs, const Batch& b, const uint8_t* accept, const int* tr_group,
