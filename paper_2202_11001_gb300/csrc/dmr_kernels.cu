@@ -440,10 +440,12 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     // few 2^-53 U W of the oracle's normals) and FP64 offsets B = -n.(a - O),
     // each rounded once to FP32.  At a voxel q = p - O of the box
     // (0 <= q < L), h(q) = fl(A.q + B) differs from the FP64 predicate by at
-    // most eps (an L + |B|) from rounding A and B, plus 3 eps (an L + |B|)
-    // from the evaluation (eps = 2^-24), plus 1.5e-14 (U W + an)(L + V) for
-    // the FP64 predicate's own rounding.  The margin takes twice the FP32
-    // part: 2^-21 (an L + |B|).
+    // most eps (an L + |B|) from rounding A and B, plus 3 eps (1 + eps)^3
+    // (an L + |B|) from the three roundings of the evaluation (each partial
+    // sum is at most (1 + eps)(an L + |B|); eps = 2^-24), plus 1.5e-14
+    // (U W + an)(L + V) for the FP64 predicate's own rounding.  The margin
+    // takes 5 eps (an L + |B|) for the FP32 part: a quarter above its bound,
+    // which covers the rounding of an, |B| and of the margin itself.
     const double N0[3] = {-((rr[0][0] + rr[1][0]) + rr[2][0]), -((rr[0][1] + rr[1][1]) + rr[2][1]),
                           -((rr[0][2] + rr[1][2]) + rr[2][2])};
     const uint32_t fp = pr.fperm[t];
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       const double Bd = -fma(nx, pick4d(vd, ia, 0), fma(ny, pick4d(vd, ia, 1), nz * pick4d(vd, ia, 2)));
       const float Ax = (float)nx, Ay = (float)ny, Az = (float)nz, Bp = (float)Bd;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
-      const float mu = (1.0f / 2097152.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
+      const float mu = (5.0f / 16777216.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
       *reinterpret_cast<float4*>(&R.fa[f][0]) = make_float4(Ax, Ay, Az, Bp);
       // fm: margin, 1/A.x, margin growth per voxel of |p - O| (landmarks),
       // and the bound on |A.x - s n_x| beyond FP32 rounding (the fused and
