@@ -534,9 +534,10 @@ enum { CF_ANY0 = 1, CF_ALL0 = 2, CF_NB_ALL0 = 4, CF_NB_NONE0 = 8, CF_NEAR = 16 }
 // certify, or a sample whose black decision needs the FP64 definition, is
 // abandoned and appended to b.slow.  FAST = false: the same item logic with
 // the careful span and the exact black decision inline, over the items of
-// b.slow, the WARPS warps of a CTA sharing one item (row batches dealt
-// round-robin, partial sums added in warp order).  Which items are handed
-// over depends only on the data, so results do not depend on the tile shape.
+// b.slow: with few such items the warps of a CTA share each item, with many
+// one warp takes an item as in the fast pass.  Which items are handed over
+// (and so the mode) depends only on the data, so results do not depend on
+// the tile shape.
 template <int ST, int WARPS, int VPL, bool FAST>
 __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM / (WARPS * 32) > 0
                                                     ? DMR_RASTER_THREADS_PER_SM / (WARPS * 32)
@@ -548,36 +549,50 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
   const int wid = threadIdx.x >> 5;
   const unsigned lemask = 0xffffffffu >> (31 - lane);
   const int n_items = 2 * b.n_tt;
+  // full-logic pass: one warp per item when the handed-over items outnumber
+  // the grid's warps, else the WARPS warps of a CTA share an item (row
+  // batches dealt round-robin, partial sums added in warp order); uniform
+  // over the grid
   __shared__ int s_item;
   __shared__ double s_part[WARPS];
   __shared__ int s_cov[WARPS];
+  const bool cta_mode = !FAST && WARPS > 1 && *(volatile unsigned*)(b.work + 1) < gridDim.x * (unsigned)WARPS;
+  const int rstep = cta_mode ? 32 * WARPS : 32;
   for (;;) {
     int item = 0;
-    if constexpr (FAST) {
-      if (lane == 0) item = (int)atomicAdd(b.work, 1u);
-      item = __shfl_sync(FULL_MASK, item, 0);
-    } else {
+    if (cta_mode) {
       if (threadIdx.x == 0) {
         const unsigned w = atomicAdd(b.work + 2, 1u);
         s_item = w < *(volatile unsigned*)(b.work + 1) ? b.slow[w] : n_items;
       }
       __syncthreads();
       item = s_item;
+    } else {
+      if (lane == 0) {
+        if constexpr (FAST) {
+          item = (int)atomicAdd(b.work, 1u);
+        } else {
+          const unsigned w = atomicAdd(b.work + 2, 1u);
+          item = w < *(volatile unsigned*)(b.work + 1) ? b.slow[w] : n_items;
+        }
+      }
+      item = __shfl_sync(FULL_MASK, item, 0);
     }
     if (item >= n_items) break;
     constexpr int NW = sizeof(ItemRec) / 16;
-    if constexpr (FAST) {
+    WarpSmem* rs = cta_mode ? (WarpSmem*)smem_raw : ws;  // whose record the warp reads
+    if (cta_mode) {
+      const int4* src = (const int4*)(b.rec + item);
+      int4* dst = (int4*)&rs->rec;
+      for (int i = threadIdx.x; i < NW; i += 32 * WARPS) dst[i] = __ldg(src + i);
+      __syncthreads();
+    } else {
       const int4* src = (const int4*)(b.rec + item);
       int4* dst = (int4*)&ws->rec;
       for (int i = lane; i < NW; i += 32) dst[i] = __ldg(src + i);
       __syncwarp();
-    } else {
-      const int4* src = (const int4*)(b.rec + item);
-      int4* dst = (int4*)&((WarpSmem*)smem_raw)->rec;
-      for (int i = threadIdx.x; i < NW; i += 32 * WARPS) dst[i] = __ldg(src + i);
-      __syncthreads();
     }
-    const ItemRec& r = FAST ? ws->rec : ((WarpSmem*)smem_raw)->rec;
+    const ItemRec& r = rs->rec;
     float sum = 0.f, comp = 0.f;
     int cov = 0;
     bool need_exact = false;  // FAST: some sample needs the FP64 black decision
@@ -619,7 +634,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
         const int yincl = warp_incl_scan(ycnt, lane);
         const int yexcl = yincl - ycnt;
         const int R = __shfl_sync(FULL_MASK, yincl, 31);
-        for (int rb = FAST ? 0 : 32 * wid; rb < R; rb += FAST ? 32 : 32 * WARPS) {
+        for (int rb = cta_mode ? 32 * wid : 0; rb < R; rb += rstep) {
           const int rr = rb + lane;
           const bool has_row = rr < R;
           const int rq = has_row ? rr : R - 1;
@@ -823,7 +838,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
         lo = lo + ol + err;
       }
       const int covt = __shfl_sync(FULL_MASK, cov, 0);  // cov is warp-uniform
-      if constexpr (FAST) {
+      if (!cta_mode) {
         if (lane == 0) {
           b.o_ssd[item] = (double)hi + (double)lo;
           b.o_cov[item] = covt;
