@@ -1000,44 +1000,53 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Trial k's deltas and objectives (one warp; lane 0 writes tr_delta and
-// tr_obj); returns the trial's sample count on every lane.
+// Trial k's deltas (one warp; lane 0 writes tr_delta and, with write_obj,
+// tr_obj); returns the trial's sample count on every lane.  GB300 issues an
+// FP64 instruction at a small fraction of the FP32 rate whatever the number
+// of active lanes, so the sums are arranged for few FP64 instructions: each
+// lane adds the per-tet differences new - old of its tets, the fold counts
+// are integers, and the two FP64 sums share one butterfly (lanes 0-15 carry
+// the dissimilarity, lanes 16-31 the deformation after the first exchange).
 __device__ __forceinline__ unsigned reduce_trial(const DevProblem& pr, const Batch& b, int k, int lane,
-                                                 int has_landmarks) {
+                                                 int has_landmarks, bool write_obj) {
   const int cand = b.tr_cand[k];
   const int first = b.tr_first[k], ntt = b.tr_ntt[k];
-  double old[3] = {0, 0, 0}, nw[3] = {0, 0, 0};
+  double ds = 0.0, dd = 0.0;
+  int dfold = 0;
   unsigned cov = 0;
   for (int j = lane; j < ntt; j += 32) {
-    int tt = first + j;
-    size_t ci = (size_t)cand * pr.ntet + b.tt_tet[tt];
-    old[0] = dadd(old[0], dadd(pr.c_ssd[2 * ci], pr.c_ssd[2 * ci + 1]));
-    old[1] = dadd(old[1], pr.c_def[ci]);
-    old[2] = dadd(old[2], (double)pr.c_fold[ci]);
-    nw[0] = dadd(nw[0], dadd(b.o_ssd[2 * (size_t)tt], b.o_ssd[2 * (size_t)tt + 1]));
-    nw[1] = dadd(nw[1], b.o_def[tt]);
-    nw[2] = dadd(nw[2], (double)b.o_fold[tt]);
+    const int tt = first + j;
+    const size_t ci = (size_t)cand * pr.ntet + b.tt_tet[tt];
+    ds = dadd(ds, dsub(dadd(b.o_ssd[2 * (size_t)tt], b.o_ssd[2 * (size_t)tt + 1]),
+                       dadd(pr.c_ssd[2 * ci], pr.c_ssd[2 * ci + 1])));
+    dd = dadd(dd, dsub(b.o_def[tt], pr.c_def[ci]));
+    dfold += b.o_fold[tt] - pr.c_fold[ci];
     cov += (unsigned)(b.o_cov[2 * (size_t)tt] + b.o_cov[2 * (size_t)tt + 1]);
   }
-  for (int q = 0; q < 3; ++q) {
-    old[q] = warp_sum_d(old[q]);
-    nw[q] = warp_sum_d(nw[q]);
-  }
+  const bool upper = lane >= 16;
+  double v = upper ? dd : ds;
+  v = dadd(v, __shfl_xor_sync(FULL_MASK, upper ? ds : dd, 16));
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = dadd(v, __shfl_xor_sync(FULL_MASK, v, o));
+  const double sum_dd = __shfl_sync(FULL_MASK, v, 16);
+  dfold = __reduce_add_sync(FULL_MASK, dfold);
   cov = __reduce_add_sync(FULL_MASK, cov);
   if (lane == 0) {
     double* dl = b.tr_delta + 4 * (size_t)k;
-    dl[0] = dsub(nw[0], old[0]);
-    dl[1] = dsub(nw[1], old[1]);
-    double gd = has_landmarks ? dl[2] : 0.0;
-    double ud = has_landmarks ? dl[3] : 0.0;
+    dl[0] = v;
+    dl[1] = sum_dd;
+    const double gd = has_landmarks ? dl[2] : 0.0;
+    const double ud = has_landmarks ? dl[3] : 0.0;
     if (!has_landmarks) dl[2] = 0.0;
-    dl[3] = dadd(dsub(nw[2], old[2]), ud);
-    const double* s = pr.sums + 4 * (size_t)cand;
-    double* ob = b.tr_obj + 4 * (size_t)k;
-    ob[0] = dadd(s[0], dl[0]) / pr.sim_norm;
-    ob[1] = dadd(s[1], dl[1]) / pr.def_norm;
-    ob[2] = pr.ng > 0 ? dadd(s[2], gd) / pr.guid_norm : 0.0;
-    ob[3] = dadd(s[3], dl[3]);
+    dl[3] = dadd((double)dfold, ud);
+    if (write_obj) {
+      const double* s = pr.sums + 4 * (size_t)cand;
+      double* ob = b.tr_obj + 4 * (size_t)k;
+      ob[0] = dadd(s[0], dl[0]) / pr.sim_norm;
+      ob[1] = dadd(s[1], dl[1]) / pr.def_norm;
+      ob[2] = pr.ng > 0 ? dadd(s[2], gd) / pr.guid_norm : 0.0;
+      ob[3] = dadd(s[3], dl[3]);
+    }
   }
   return cov;
 }
@@ -1047,7 +1056,7 @@ __global__ void k_reduce_partial(const DevProblem* probs, Batch b, int has_landm
   int lane = threadIdx.x & 31;
   if (k >= b.n_trials) return;
   const DevProblem& pr = probs[b.tr_prob ? b.tr_prob[k] : 0];
-  const unsigned cov = reduce_trial(pr, b, k, lane, has_landmarks);
+  const unsigned cov = reduce_trial(pr, b, k, lane, has_landmarks, true);
   if (lane == 0) atomicAdd(pr.samples, (unsigned long long)cov);
 }
 
@@ -1058,13 +1067,19 @@ void launch_reduce_partial(const DevProblem* probs, const Batch& b, cudaStream_t
 }
 
 // Accept-if-improves (Sec. 2.2), constraint domination first.
+// The objectives are the raw sums over positive constants, so the trial is
+// compared with the candidate in sums (after the deltas of reduce_trial):
+// constraint domination first, then weak Pareto dominance with one strict
+// improvement.
 __device__ __forceinline__ bool accept_trial(const DevProblem& pr, const Batch& b, int k) {
   const double* s = pr.sums + 4 * (size_t)b.tr_cand[k];
-  const double* o = b.tr_obj + 4 * (size_t)k;
-  double cur[4] = {s[0] / pr.sim_norm, s[1] / pr.def_norm, pr.ng > 0 ? s[2] / pr.guid_norm : 0.0, s[3]};
-  if (o[3] != cur[3]) return o[3] < cur[3];
-  bool le = o[0] <= cur[0] && o[1] <= cur[1] && o[2] <= cur[2];
-  bool lt = o[0] < cur[0] || o[1] < cur[1] || o[2] < cur[2];
+  const double* dl = b.tr_delta + 4 * (size_t)k;
+  const double n3 = dadd(s[3], dl[3]);
+  if (n3 != s[3]) return n3 < s[3];
+  const double n0 = dadd(s[0], dl[0]), n1 = dadd(s[1], dl[1]);
+  const double n2 = pr.ng > 0 ? dadd(s[2], dl[2]) : s[2];
+  const bool le = n0 <= s[0] && n1 <= s[1] && n2 <= s[2];
+  const bool lt = n0 < s[0] || n1 < s[1] || n2 < s[2];
   return le && lt;
 }
 
@@ -1133,17 +1148,26 @@ __global__ void k_commit_sums(const DevProblem* probs, Batch b, const uint8_t* a
   if (j1 <= j0) return;
   int k0 = cand_trials[j0];
   const DevProblem& pr = probs[b.tr_prob ? b.tr_prob[k0] : 0];
-  double tot[4] = {0, 0, 0, 0};
-  for (int jb = j0; jb < j1; jb += 32) {
-    int j = jb + lane;
-    double d[4] = {0, 0, 0, 0};
-    if (j < j1) {
-      int k = cand_trials[j];
-      if (accept[k])
-        for (int q = 0; q < 4; ++q) d[q] = b.tr_delta[4 * (size_t)k + q];
-    }
-    for (int q = 0; q < 4; ++q) tot[q] = dadd(tot[q], warp_sum_d(d[q]));
+  // each lane adds its accepted trials' deltas, then one butterfly carries
+  // all four sums (lanes 0-7, 8-15, 16-23, 24-31 end with delta 0, 1, 2, 3):
+  // few FP64 instructions
+  double d[4] = {0, 0, 0, 0};
+  for (int j = j0 + lane; j < j1; j += 32) {
+    const int k = cand_trials[j];
+    if (accept[k])
+      for (int q = 0; q < 4; ++q) d[q] = dadd(d[q], b.tr_delta[4 * (size_t)k + q]);
   }
+  const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+  const double a0 = dadd(up16 ? d[2] : d[0], __shfl_xor_sync(FULL_MASK, up16 ? d[0] : d[2], 16));
+  const double a1 = dadd(up16 ? d[3] : d[1], __shfl_xor_sync(FULL_MASK, up16 ? d[1] : d[3], 16));
+  double v = dadd(up8 ? a1 : a0, __shfl_xor_sync(FULL_MASK, up8 ? a0 : a1, 8));
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v = dadd(v, __shfl_xor_sync(FULL_MASK, v, o));
+  double tot[4];
+  tot[0] = __shfl_sync(FULL_MASK, v, 0);
+  tot[1] = __shfl_sync(FULL_MASK, v, 8);
+  tot[2] = __shfl_sync(FULL_MASK, v, 16);
+  tot[3] = __shfl_sync(FULL_MASK, v, 24);
   if (lane == 0) {
     double* s = pr.sums + 4 * (size_t)b.tr_cand[k0];
     for (int q = 0; q < 4; ++q) s[q] = dadd(s[q], tot[q]);
@@ -1168,7 +1192,7 @@ __global__ void __launch_bounds__(256) k_reduce_commit(const DevProblem* probs, 
   const DevProblem& pr = probs[pi];
   unsigned cov = 0;
   if (k < b.n_trials) {
-    cov = reduce_trial(pr, b, k, lane, has_landmarks);
+    cov = reduce_trial(pr, b, k, lane, has_landmarks, false);
     int acc = 0;
     if (lane == 0) {
       acc = accept_trial(pr, b, k) ? 1 : 0;
