@@ -470,19 +470,21 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       *reinterpret_cast<float4*>(&R.fm[f][0]) = make_float4(
           mu, 1.0f / Ax, (1.0f / 2097152.0f) * an + 1.5e-14f * (UW + an), 3.0e-14f * UW + 1e-30f);
     }
-    // FP32 map relative to the origins: p'_rel = vr + G vr + k
+    // FP32 map relative to the origins: p'_rel = vr + G vr + k, G rounded
+    // once from the FP64 map, k = (O - Op) + d0 + G (O - own_0) in FP32 from
+    // the FP64 differences rounded once (its error, a few eps M, stays well
+    // inside the black-decision margin 2^-19 M with the evaluation's own)
     float G[3][4];
     float gmax = 0.f, kmax = 0.f;
+    const float oo0 = (float)dsub((double)O[0], own[0][0]), oo1 = (float)dsub((double)O[1], own[0][1]),
+                oo2 = (float)dsub((double)O[2], own[0][2]);
     for (int c = 0; c < 3; ++c) {
-      const double oo0 = dsub((double)O[0], own[0][0]), oo1 = dsub((double)O[1], own[0][1]),
-                   oo2 = dsub((double)O[2], own[0][2]);
-      const double d0 = dsub(par[0][c], own[0][c]);
-      const double kk = ((double)(O[c] - Op[c]) + d0) + fma(Gd[c][0], oo0, fma(Gd[c][1], oo1, Gd[c][2] * oo2));
       for (int j = 0; j < 3; ++j) {
         G[c][j] = (float)Gd[c][j];
         gmax = fmaxf(gmax, fabsf(G[c][j]));
       }
-      G[c][3] = (float)kk;
+      const float d0 = (float)dsub(par[0][c], own[0][c]);
+      G[c][3] = ((float)(O[c] - Op[c]) + d0) + fmaf(G[c][0], oo0, fmaf(G[c][1], oo1, G[c][2] * oo2));
       kmax = fmaxf(kmax, fabsf(G[c][3]));
       *reinterpret_cast<float4*>(&R.G[c][0]) = make_float4(G[c][0], G[c][1], G[c][2], G[c][3]);
     }
