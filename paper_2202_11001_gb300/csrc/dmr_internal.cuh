@@ -74,7 +74,8 @@ struct DevProblem {
 // integer origins O (own) and Op (partner).
 struct __align__(16) ItemRec {
   int flags;        // bit0: rasterise (6V_own > 0); bit1: clamp-free map; bit2 / bit3: every
-                    // partner voxel a sample of this item can reach is 0 / is not 0
+                    // partner voxel a sample of this item can reach is 0 / is not 0; bit4 (with
+                    // bit2): the own voxels are 0 too
   int prob;
   int tet;
   int dir;

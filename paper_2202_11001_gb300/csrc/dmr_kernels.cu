@@ -335,6 +335,20 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       const long nzc = nz_in_box(pr.nzsat[1 - d], np, q0, q1);
       const long vol = (long)(q1[0] - q0[0] + 1) * (q1[1] - q0[1] + 1) * (q1[2] - q0[2] + 1);
       zbits[d] = (nzc == 0 ? 4 : 0) | (nzc == vol ? 8 : 0);
+      // bit4 (with bit2): the own image is 0 over the own tet's box too, so
+      // every sample is 0 against 0 (d^2 = 0, black or not): only the
+      // coverage is counted
+      const int* no = pr.n[d];
+      if ((zbits[d] & 4) && mfin[d] && pr.nzsat[d]) {
+        int o0[3], o1[3];
+        bool empty = false;
+        for (int a = 0; a < 3; ++a) {
+          o0[a] = (int)fminf(fmaxf(ceilf(mlo[d][a]), 0.0f), (float)(no[a] - 1));
+          o1[a] = (int)fminf(fmaxf(floorf(mhi[d][a]), 0.0f), (float)(no[a] - 1));
+          empty = empty || o0[a] > o1[a];
+        }
+        if (!empty && nz_in_box(pr.nzsat[d], no, o0, o1) == 0) zbits[d] |= 16;
+      }
     }
   }
 
