@@ -116,6 +116,33 @@ def test_ellipsoid64_black_rule_off():
         assert_terms_match(g, o, c)
 
 
+@pytest.mark.parametrize("which", ["both", "source", "target"])
+@pytest.mark.parametrize("black", [True, False])
+def test_zero_images_empty_space_paths(which, black):
+    """Images that are all 0 on one or both sides: every item takes an
+    empty-space path (partner region all 0, with or without the own box all 0)
+    or its complement; coverage exact, objectives against the oracle, then one
+    wave of partial evaluations."""
+    pr = synth.sphere_pair(seed=7, C=4)
+    src, tgt = pr["img"]
+    if which in ("both", "source"):
+        src = np.zeros_like(src)
+    if which in ("both", "target"):
+        tgt = np.zeros_like(tgt)
+    pr = dict(pr, img=(src, tgt))
+    g, o = make_pair(pr, black=black)
+    assert_obj_close(g.eval_full(pr["coords"]), o.eval_full(pr["coords"]))
+    for c in range(4):
+        assert_terms_match(g, o, c)
+    groups = synth.single_point_fos(pr["mesh"])
+    g.set_fos(groups)
+    w = g.waves()[0]
+    gids = np.repeat(w, 4).astype(np.int32)
+    cids = np.tile(np.arange(4), len(w)).astype(np.int32)
+    tc = synth.trial_coords(pr["coords"], groups, gids, cids, 0.4, pr["mesh"], np.random.default_rng(9))
+    assert_obj_close(g.eval_partial(gids, cids, tc), o.eval_partial(groups, gids, cids, tc), what="trial objectives")
+
+
 def test_plan_generation_matches_sequential_and_oracle():
     """The CUDA-graph generation plan (propose, partial evaluation,
     accept-if-improves, commit for every wave) equals the same steps through
