@@ -243,8 +243,12 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
   // edge differences target - source (direction 0's D; direction 1 uses -D,
   // exactly, since a - b = -(b - a) in round-to-nearest)
   double Dm[3][3];
+  float Dmf[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int a = 0; a < 3; ++a) Dm[i][a] = dsub(e[1][i][a], e[0][i][a]);
+    for (int a = 0; a < 3; ++a) {
+      Dm[i][a] = dsub(e[1][i][a], e[0][i][a]);
+      Dmf[i][a] = (float)Dm[i][a];
+    }
 
   // deformation (FP32 from FP64 edge vectors and their differences)
   double def = 0.0;
@@ -373,10 +377,9 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
         xp[q] = make_double2(par[i0][a0], par[i1][a1]);
       }
     }
-    // map G = [D1 D2 D3][r1; r2; r3] / det for the FP32 path, with fused
-    // multiply-adds (within a few FP64 ulps of the exact-order map, which
-    // the decisions that need it rebuild from X and XP); det = 6V_own
-    const double sg = d == 0 ? 1.0 : -1.0;
+    // adjugate rows of the own edge matrix (FP64, fused; they give the face
+    // normals below and, rounded, the FP32 map; the decisions that need the
+    // exact-order map rebuild it from X and XP); det = 6V_own
     double rr[3][3];
     for (int j = 0; j < 3; ++j) rr[0][j] = r0[d][j];
     rr[1][0] = fma(eo[2][1], eo[0][2], -eo[2][2] * eo[0][1]);
@@ -385,16 +388,31 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     rr[2][0] = fma(eo[0][1], eo[1][2], -eo[0][2] * eo[1][1]);
     rr[2][1] = fma(eo[0][2], eo[1][0], -eo[0][0] * eo[1][2]);
     rr[2][2] = fma(eo[0][0], eo[1][1], -eo[0][1] * eo[1][0]);
-    const double inv = sg / vol6[d];
-    double Gd[3][3];
-    for (int c = 0; c < 3; ++c)
-      for (int j = 0; j < 3; ++j) Gd[c][j] = fma(Dm[0][c], rr[0][j], fma(Dm[1][c], rr[1][j], Dm[2][c] * rr[2][j])) * inv;
+    // FP32 map G = [D1 D2 D3][r1; r2; r3] / det from the FP64 edge
+    // differences and adjugate rows rounded once: an entry differs from the
+    // exact map by at most 8 eps gabs, gabs = max over (c, j) of
+    // sum_i |D_ic r_ij| / |det| (>= |G|), which M below takes in place of max |G|
+    float G[3][4];
+    float gabs = 0.f;
+    {
+      const float invf = (d == 0 ? 1.0f : -1.0f) / (float)vol6[d];
+      const float ainv = fabsf(invf);
+      float rf[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) rf[i][j] = (float)rr[i][j];
+      for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 3; ++j) {
+          G[c][j] = fmaf(Dmf[0][c], rf[0][j], fmaf(Dmf[1][c], rf[1][j], Dmf[2][c] * rf[2][j])) * invf;
+          const float ga = (fabsf(Dmf[0][c] * rf[0][j]) + fabsf(Dmf[1][c] * rf[1][j]) + fabsf(Dmf[2][c] * rf[2][j])) * ainv;
+          gabs = fmaxf(gabs, ga);
+        }
+    }
     // linear-elastic energy from the source->target map (direction 0)
     if (d == 0 && pr.model == 1 && vol6[0] != 0.0 && isfinite(vol6[0])) {
       float H[3][3];
       for (int c = 0; c < 3; ++c)
         for (int j = 0; j < 3; ++j) {
-          float g = (float)Gd[c][j] * pr.sp[1][c] / pr.sp[0][j];
+          float g = G[c][j] * pr.sp[1][c] / pr.sp[0][j];
           if (c == j) g += pr.sp[1][c] / pr.sp[0][c] - 1.0f;
           H[c][j] = g;
         }
@@ -484,25 +502,25 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       *reinterpret_cast<float4*>(&R.fm[f][0]) = make_float4(
           mu, 1.0f / Ax, (1.0f / 2097152.0f) * an + 1.5e-14f * (UW + an), 3.0e-14f * UW + 1e-30f);
     }
-    // FP32 map relative to the origins: p'_rel = vr + G vr + k, G rounded
-    // once from the FP64 map, k = (O - Op) + d0 + G (O - own_0) in FP32 from
-    // the FP64 differences rounded once (its error, a few eps M, stays well
-    // inside the black-decision margin 2^-19 M with the evaluation's own)
-    float G[3][4];
+    // FP32 map relative to the origins: p'_rel = vr + G vr + k with
+    // k = (O - Op) + d0 + G (O - own_0) in FP32 from the FP64 differences
+    // rounded once.  Errors against the exact map at a box voxel v: G's, at
+    // most 8 eps gabs per entry (rounding D, r and det, the products and
+    // sums, the scaling), enter through G (v - own_0) with |v - own_0| <= L
+    // per axis, so at most 8 eps M (M >= 3 gabs L); k's own roundings a few
+    // eps M; the evaluation's ~7 eps M: inside the black-decision margin
+    // 2^-19 M = 32 eps M
     float gmax = 0.f, kmax = 0.f;
     const float oo0 = (float)dsub((double)O[0], own[0][0]), oo1 = (float)dsub((double)O[1], own[0][1]),
                 oo2 = (float)dsub((double)O[2], own[0][2]);
     for (int c = 0; c < 3; ++c) {
-      for (int j = 0; j < 3; ++j) {
-        G[c][j] = (float)Gd[c][j];
-        gmax = fmaxf(gmax, fabsf(G[c][j]));
-      }
+      for (int j = 0; j < 3; ++j) gmax = fmaxf(gmax, fabsf(G[c][j]));
       const float d0 = (float)dsub(par[0][c], own[0][c]);
       G[c][3] = ((float)(O[c] - Op[c]) + d0) + fmaf(G[c][0], oo0, fmaf(G[c][1], oo1, G[c][2] * oo2));
       kmax = fmaxf(kmax, fabsf(G[c][3]));
       *reinterpret_cast<float4*>(&R.G[c][0]) = make_float4(G[c][0], G[c][1], G[c][2], G[c][3]);
     }
-    float M = (float)L * (1.0f + 3.0f * gmax) + kmax + 2.0f;
+    float M = (float)L * (1.0f + 3.0f * fmaxf(gmax, gabs)) + kmax + 2.0f;
     // bit1: the partner tet lies within [-0.75, n - 0.25] on every axis and
     // the FP32 map error bound is far below 0.25 voxel, so no mapped voxel
     // coordinate of this tet can leave [-1, n].  fminf/fmaxf skip NaN, so
