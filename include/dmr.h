@@ -203,9 +203,11 @@ int dmr_plan_destroy(dmr_plan* plan);
 /* Kernel launches per dmr_plan_run (for accounting). */
 int dmr_plan_launches(const dmr_plan* plan, int* launches);
 /* Device time of the last completed dmr_plan_run, summed over its waves, of
- * the geometry set-up kernels and of the rasterise-and-sample kernels (CUDA
- * events recorded inside the graph, on the problem's stream).  Call after
- * that run has finished (e.g. after synchronising the stream). */
+ * the rasterise-and-sample kernels (CUDA events recorded inside the graph
+ * around them, on the problem's stream; each recorded event costs the graph a
+ * few microseconds, so only these are recorded).  *setup_ms is set to -1 (not
+ * timed).  Call after that run has finished (e.g. after synchronising the
+ * stream). */
 int dmr_plan_kernel_ms(const dmr_plan* plan, float* setup_ms, float* raster_ms);
 
 /* Tile shape of the rasterise-and-sample kernel: warps per CTA (4, 8, 16)

@@ -1407,7 +1407,7 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
     dmr_plan_destroy(pl);
     return fail(DMR_ECUDA, "plan upload failed");
   }
-  pl->ev.assign(3 * (size_t)nw, nullptr);
+  pl->ev.assign(2 * (size_t)nw, nullptr);
   for (auto& e : pl->ev)
     if (cudaEventCreate(&e) != cudaSuccess) {
       dmr_plan_destroy(pl);
@@ -1451,12 +1451,11 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
     b.aff_n = any_ng ? pl->sc.aff_n : nullptr;
     const int* trg = pl->tr_group + w_tr0[w];
     launch_propose(d_probs, b, trg, d_gptr, d_gpts, pl->deltas + (size_t)w_tr0[w] * dl_per, cs);
-    cudaEventRecordWithFlags(pl->ev[3 * w], cs, cudaEventRecordExternal);
     launch_setup(d_probs, b, cs);
-    cudaEventRecordWithFlags(pl->ev[3 * w + 1], cs, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(pl->ev[2 * w], cs, cudaEventRecordExternal);
     launch_raster(d_probs, b, p0->storage, p0->warps, p0->vpw, p0->n_sm, cs, any_ng ? cs2 : nullptr,
                   any_ng ? ev_fork : nullptr);
-    cudaEventRecordWithFlags(pl->ev[3 * w + 2], cs, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(pl->ev[2 * w + 1], cs, cudaEventRecordExternal);
     launches += 2 + kRasterLaunches;
     if (any_ng) {
       // the fork is recorded inside launch_raster before the fast kernel
@@ -1635,15 +1634,13 @@ int dmr_plan_run(dmr_plan* pl) {
 
 int dmr_plan_kernel_ms(const dmr_plan* pl, float* setup_ms, float* raster_ms) {
   if (!pl) return fail(DMR_EINVAL, "null plan");
-  float su = 0.f, ra = 0.f;
-  for (size_t w = 0; w + 2 < pl->ev.size(); w += 3) {
-    float a = 0.f, b = 0.f;
-    CU(cudaEventElapsedTime(&a, pl->ev[w], pl->ev[w + 1]));
-    CU(cudaEventElapsedTime(&b, pl->ev[w + 1], pl->ev[w + 2]));
-    su += a;
+  float ra = 0.f;
+  for (size_t w = 0; w + 1 < pl->ev.size(); w += 2) {
+    float b = 0.f;
+    CU(cudaEventElapsedTime(&b, pl->ev[w], pl->ev[w + 1]));
     ra += b;
   }
-  if (setup_ms) *setup_ms = su;
+  if (setup_ms) *setup_ms = -1.f;
   if (raster_ms) *raster_ms = ra;
   return DMR_OK;
 }

@@ -488,7 +488,8 @@ class Plan:
         _check(self.prob._lib.dmr_plan_update(self.h, ctypes.addressof(ptrs)))
 
     def kernel_ms(self):
-        """(set-up ms, raster ms) of the last completed run."""
+        """(set-up ms, raster ms) of the last completed run; set-up is -1 (not
+        timed: only the raster kernels carry timing events)."""
         su, ra = ctypes.c_float(), ctypes.c_float()
         _check(self.prob._lib.dmr_plan_kernel_ms(self.h, ctypes.addressof(su), ctypes.addressof(ra)))
         return su.value, ra.value
