@@ -676,6 +676,12 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           if constexpr (FAST) {
             if (__any_sync(FULL_MASK, careful)) goto handover;
           }
+          if ((*(volatile int*)&r.flags & 20) == 20) {
+            // own and partner voxels all 0: every sample adds 0, only the
+            // batch's voxel count matters
+            cov += __reduce_add_sync(FULL_MASK, (unsigned)xcnt);
+            continue;
+          }
           const unsigned nzm = __ballot_sync(FULL_MASK, xcnt > 0);
           const int cidx = __popc(nzm & (lemask >> 1));
           const int xincl = warp_incl_scan(xcnt, lane);
