@@ -711,11 +711,10 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           float bsum = 0.f;
           if (pzero) {
             // every partner voxel these samples can reach is 0: each sample is
-            // 0 and black, so only the own image is read (and not even that
-            // when the own voxels are all 0 too: every sample adds 0).  Same
-            // per-lane order and fold points as the loop below (identical sums).
-            const int Tz = (*(volatile int*)&r.flags & 16) ? 0 : T;
-            for (int vb = 0; vb < Tz; vb += 32) {
+            // 0 and black, so only the own image is read (items whose own
+            // voxels are all 0 as well never get here).  Same per-lane order
+            // and fold points as the loop below (identical sums).
+            for (int vb = 0; vb < T; vb += 32) {
               if (vb != 0 && (vb & 255) == 0) {
                 const float yk = bsum - comp;
                 const float tk = sum + yk;
