@@ -1423,13 +1423,15 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
   // side branch of the graph: landmark relocation needs only the set-up
   // records, so it runs beside the raster kernels
   cudaStream_t cs2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sums = nullptr;
   if (cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_sums, cudaEventDisableTiming) != cudaSuccess) {
     if (cs2) cudaStreamDestroy(cs2);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_sums) cudaEventDestroy(ev_sums);
     cudaStreamDestroy(cs);
     dmr_plan_destroy(pl);
     return fail(DMR_ECUDA, "stream create failed");
@@ -1464,10 +1466,18 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
       cudaStreamWaitEvent(cs, ev_join, 0);
       ++launches;
     }
+    // with guidance points the side stream orders the sums of wave w before
+    // the next wave's landmark kernel (which rewrites the delta buffer), and
+    // the next wave's reduce waits for that landmark kernel
     launch_reduce_commit(d_probs, b, pl->sc.accept, trg, d_gptr, d_gpts, pl->cand_ptr + w_c0[w],
-                         pl->cand_trials + w_tr0[w], w_nlist[w], cs);
+                         pl->cand_trials + w_tr0[w], w_nlist[w], cs, any_ng ? cs2 : nullptr,
+                         any_ng ? ev_sums : nullptr);
     launches += 2;
     e = cudaGetLastError();
+  }
+  if (any_ng) {
+    cudaEventRecord(ev_join, cs2);
+    cudaStreamWaitEvent(cs, ev_join, 0);
   }
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
@@ -1475,6 +1485,7 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
   cudaStreamDestroy(cs2);
   cudaEventDestroy(ev_fork);
   cudaEventDestroy(ev_join);
+  cudaEventDestroy(ev_sums);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
     dmr_plan_destroy(pl);

@@ -166,10 +166,12 @@ void launch_commit(const DevProblem* probs, const Batch& b, const uint8_t* accep
                    const int* g_ptr, const int* g_pts, const int* cand_ptr, const int* cand_trials, int n_list,
                    cudaStream_t st);
 // Plans: reduce + accept + per-trial commit fused, then the per-candidate sums
-// (two launches instead of five).
+// (two launches instead of five).  With a side stream the sums kernel runs
+// there, after `sums_ev` is recorded on `st`: beside the next wave's proposal
+// and set-up, which neither read nor write what it touches.
 void launch_reduce_commit(const DevProblem* probs, const Batch& b, uint8_t* accept, const int* tr_group,
                           const int* g_ptr, const int* g_pts, const int* cand_ptr, const int* cand_trials, int n_list,
-                          cudaStream_t st);
+                          cudaStream_t st, cudaStream_t sums_st = nullptr, cudaEvent_t sums_ev = nullptr);
 void launch_propose(const DevProblem* probs, const Batch& b, const int* tr_group, const int* g_ptr, const int* g_pts,
                     const double* deltas, cudaStream_t st);
 

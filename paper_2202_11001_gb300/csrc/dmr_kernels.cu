@@ -1285,12 +1285,18 @@ __global__ void __launch_bounds__(256) k_reduce_commit(const DevProblem* probs, 
 
 void launch_reduce_commit(const DevProblem* probs, const Batch& b, uint8_t* accept, const int* tr_group,
                           const int* g_ptr, const int* g_pts, const int* cand_ptr, const int* cand_trials, int n_list,
-                          cudaStream_t st) {
+                          cudaStream_t st, cudaStream_t sums_st, cudaEvent_t sums_ev) {
   if (b.n_trials <= 0) return;
   const long threads = 32L * b.n_trials;
   k_reduce_commit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(probs, b, b.aff_n != nullptr, accept, tr_group,
                                                                       g_ptr, g_pts);
-  k_commit_sums<<<(unsigned)((32L * n_list + 255) / 256), 256, 0, st>>>(probs, b, accept, cand_ptr, cand_trials, n_list);
+  cudaStream_t ss = st;
+  if (sums_st && sums_ev) {
+    cudaEventRecord(sums_ev, st);
+    cudaStreamWaitEvent(sums_st, sums_ev, 0);
+    ss = sums_st;
+  }
+  k_commit_sums<<<(unsigned)((32L * n_list + 255) / 256), 256, 0, ss>>>(probs, b, accept, cand_ptr, cand_trials, n_list);
 }
 
 void launch_commit(const DevProblem* probs, const Batch& b, const uint8_t* accept, const int* tr_group,
