@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one fast raster-pass launch (one wave of the
 # generation), from the ncu capture summarised in profiles/raster_fast_ellipsoid64.md;
 # None for workloads without a capture of the current kernel.
-FAST_PASS_DRAM_BYTES = {("ellipsoid64", "f32"): 76.28e6}
+FAST_PASS_DRAM_BYTES = {("ellipsoid64", "f32"): 75.46e6}
 
 
 def reduce_over_ranks(total_s, samples, dist, device):
@@ -527,6 +527,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--generations", default="300,600", help="cube_multires: generations per level")
+    ap.add_argument("--tile", default="", help="fixed raster tile WARPSxVOXELS (e.g. 4x32) instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3")
@@ -571,7 +572,13 @@ def main():
         return g, groups
 
     g, groups = build(args.storage)
-    tile_w, tile_v, tile_table = g.autotune()
+    if args.tile:
+        # a fixed tile (no autotuning): reproducible profiling of one kernel instance
+        tile_w, tile_v = (int(v) for v in args.tile.lower().split("x"))
+        g.set_tile(tile_w, tile_v)
+        tile_table = {}
+    else:
+        tile_w, tile_v, tile_table = g.autotune()
     waves = g.waves()
     rng = np.random.default_rng(100 + rank)
     deltas = deltas_for(pr, groups, C, rng)
