@@ -59,7 +59,8 @@ enum {
   DMR_EINVAL = -1,   /* bad argument or size */
   DMR_ENOMEM = -2,   /* device or host allocation failed */
   DMR_ECUDA = -3,    /* a CUDA runtime call failed */
-  DMR_ETIMEOUT = -4, /* reserved: a bounded device wait gave up */
+  DMR_ETIMEOUT = -4, /* a bounded device wait gave up: returned by the dmr_mlp_*
+                        calls when a tensor-core completion wait runs out */
   DMR_ESTATE = -5    /* call out of order (e.g. commit before eval_partial) */
 };
 
@@ -225,20 +226,22 @@ int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, flo
 
 /* Full evaluation of ONE candidate that allocates no memory.  The paper has
  * no counterpart; this is a service for callers that must not allocate at
- * evaluation time: code running while a stream is captured into a CUDA graph
- * (cudaMalloc is not permitted during capture), optimiser loops that cannot
- * afford the device synchronisation cudaMalloc/cudaFree imply, and processes
- * whose device memory is owned by another allocator.
+ * evaluation time: optimiser loops that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree imply, and processes whose device
+ * memory is owned by another allocator (a caching allocator or a pool that
+ * holds the whole budget), where a library-side cudaMalloc would fail.
  * coords: device [2][3][P] FP64 (both meshes of the candidate); obj_out:
  * device [4] FP64, the same four values dmr_eval_full gives.  Limits:
- * N_tet <= 4608 and n_guide <= 512, else DMR_EINVAL.  The problem's images,
+ * N_tet <= 4608 and n_guide <= 512, else DMR_EINVAL; the problem must
+ * belong to the current device, else DMR_EINVAL.  The problem's images,
  * topology and population state are only read; the scratch is one fixed
- * array of about 6.3 MB that every device holds from the first call until
- * the process exits.  The first call on a device looks that array up
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
- * calls share the array: calls that may overlap on the GPU (other streams,
- * other threads) race and must be serialised by the caller.  Work is
- * enqueued on the problem's stream; the call does not wait for it. */
+ * array of about 5.6 MB that every device holds from the library's load
+ * until the process exits.  The first call on a device looks that array's
+ * address up (cudaGetSymbolAddress) and should come before any stream
+ * capture.  All calls share the array: calls that may overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the
+ * caller.  Work is enqueued on the problem's stream; the call does not wait
+ * for it. */
 int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double* obj_out);
 
 /* The paper's folding check (Sec. 2.3.4), as a cross-check of the signed

@@ -13,6 +13,18 @@ p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
 Parameters are held in the flat layout the CUDA library uses:
 [W1 (128x256), b1 (128), W2 (128x128), b2, W3 (128x128), b3, W4 (16x128), b4 (16)],
 weights as [out][in]; rows 6..15 of W4 and b4[6:] are padding and stay 0.
+
+Precision.  The network is specified with BF16 weights and FP32 accumulation.
+A BF16 x BF16 tensor-core product takes both operands in BF16, so with
+``bf16_operands=True`` every matrix-product operand is rounded to BF16 (8
+significant bits, round to nearest, ties to even) before an exact FP64
+product: the weights, each hidden activation H_l, and in the backward pass
+each back-propagated error dZ_l where it enters a product (dW_l = dZ_l^T in,
+dH_{l-1} = dZ_l W_l).  Biases, pre-activations, GELU, the loss and the bias
+gradients (column sums of dZ_l) stay unrounded.  With the default
+``bf16_operands=False`` everything is plain FP64.
+
+Test infrastructure only: the CUDA library never imports this module.
 """
 import math
 
@@ -40,6 +52,14 @@ def pack(d):
     return np.concatenate([np.asarray(d[name], np.float64).reshape(-1) for name, _ in SHAPES])
 
 
+def round_bf16(x):
+    """Round to the nearest BF16 value (8 significant bits, ties to even),
+    from the definition: x = m 2^e with 0.5 <= |m| < 1, keep m to 2^-8."""
+    x = np.asarray(x, np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0), e - 8)
+
+
 def gelu(z):
     return 0.5 * z * (1.0 + np.tanh(_C * (z + _A * z ** 3)))
 
@@ -49,29 +69,37 @@ def gelu_grad(z):
     return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * _C * (1.0 + 3.0 * _A * z * z)
 
 
-def forward(params, X):
+def forward(params, X, bf16_operands=False):
     p = unpack(params)
-    X = np.asarray(X, np.float64)
-    Z1 = X @ p["W1"].T + p["b1"]
-    H1 = gelu(Z1)
-    Z2 = H1 @ p["W2"].T + p["b2"]
-    H2 = gelu(Z2)
-    Z3 = H2 @ p["W3"].T + p["b3"]
-    H3 = gelu(Z3)
-    Z4 = H3 @ p["W4"].T + p["b4"]
-    return Z4[:, :OUT], dict(X=X, Z1=Z1, H1=H1, Z2=Z2, H2=H2, Z3=Z3, H3=H3)
+    q = round_bf16 if bf16_operands else (lambda a: a)
+    X = q(np.asarray(X, np.float64))
+    W = [q(p["W1"]), q(p["W2"]), q(p["W3"]), q(p["W4"])]
+    Z1 = X @ W[0].T + p["b1"]
+    H1 = q(gelu(Z1))
+    Z2 = H1 @ W[1].T + p["b2"]
+    H2 = q(gelu(Z2))
+    Z3 = H2 @ W[2].T + p["b3"]
+    H3 = q(gelu(Z3))
+    Z4 = H3 @ W[3].T + p["b4"]
+    return Z4[:, :OUT], dict(X=X, Z1=Z1, H1=H1, Z2=Z2, H2=H2, Z3=Z3, H3=H3, W=W)
 
 
-def loss(params, X, Y):
-    out, _ = forward(params, X)
+def loss(params, X, Y, bf16_operands=False):
+    out, _ = forward(params, X, bf16_operands)
     mu, s = out[:, :3], out[:, 3:6]
     return float(np.mean(np.sum(0.5 * ((Y - mu) ** 2 * np.exp(-s) + s), axis=1)))
 
 
-def grad(params, X, Y):
-    """Analytic gradient of ``loss`` (backpropagation through the 4 layers)."""
-    p = unpack(params)
-    out, c = forward(params, X)
+def grad(params, X, Y, bf16_operands=False, magnitudes=False):
+    """Analytic gradient of ``loss`` (backpropagation through the 4 layers).
+
+    With ``magnitudes=True`` also returns, in the same flat layout, the sum of
+    absolute products that forms each entry (sum over rows of |dZ| |input| for
+    a weight, of |dZ| for a bias): the scale at which operand rounding in the
+    product acts on that entry."""
+    q = round_bf16 if bf16_operands else (lambda a: a)
+    out, c = forward(params, X, bf16_operands)
+    W = c["W"]
     B = X.shape[0]
     mu, s = out[:, :3], out[:, 3:6]
     r = Y - mu
@@ -79,24 +107,23 @@ def grad(params, X, Y):
     dZ4 = np.zeros((B, OUTP))
     dZ4[:, :3] = -r * e / B
     dZ4[:, 3:6] = 0.5 * (1.0 - r * r * e) / B
-    g = {}
-    g["W4"] = dZ4.T @ c["H3"]
-    g["b4"] = dZ4.sum(axis=0)
-    dH3 = dZ4 @ p["W4"]
-    dZ3 = dH3 * gelu_grad(c["Z3"])
-    g["W3"] = dZ3.T @ c["H2"]
-    g["b3"] = dZ3.sum(axis=0)
-    dH2 = dZ3 @ p["W3"]
-    dZ2 = dH2 * gelu_grad(c["Z2"])
-    g["W2"] = dZ2.T @ c["H1"]
-    g["b2"] = dZ2.sum(axis=0)
-    dH1 = dZ2 @ p["W2"]
-    dZ1 = dH1 * gelu_grad(c["Z1"])
-    g["W1"] = dZ1.T @ c["X"]
-    g["b1"] = dZ1.sum(axis=0)
-    g["W4"][OUT:] = 0.0
-    g["b4"][OUT:] = 0.0
-    return pack(g)
+    g, mag = {}, {}
+    ins = {1: c["X"], 2: c["H1"], 3: c["H2"], 4: c["H3"]}
+    zs = {1: c["Z1"], 2: c["Z2"], 3: c["Z3"]}
+    dZ = dZ4
+    for layer in (4, 3, 2, 1):
+        dZq = q(dZ)
+        g["W%d" % layer] = dZq.T @ ins[layer]
+        g["b%d" % layer] = dZ.sum(axis=0)
+        mag["W%d" % layer] = np.abs(dZq).T @ np.abs(ins[layer])
+        mag["b%d" % layer] = np.abs(dZ).sum(axis=0)
+        if layer > 1:
+            dH = dZq @ W[layer - 1]
+            dZ = dH * gelu_grad(zs[layer - 1])
+    for d in (g, mag):
+        d["W4"][OUT:] = 0.0
+        d["b4"][OUT:] = 0.0
+    return (pack(g), pack(mag)) if magnitudes else pack(g)
 
 
 def adam_step(params, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

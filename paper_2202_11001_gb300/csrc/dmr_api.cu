@@ -390,6 +390,8 @@ int problem_view(const ::dmr_problem* p, DevProblem* hp, int* storage, int* warp
 
 const DevProblem* problem_device(const ::dmr_problem* p) { return p ? p->d_prob : nullptr; }
 
+int problem_device_id(const ::dmr_problem* p) { return p ? p->dev : -1; }
+
 }  // namespace dmr
 
 extern "C" {

@@ -182,5 +182,7 @@ int set_error(int code, const std::string& msg);
 int problem_view(const ::dmr_problem* p, DevProblem* hp, int* storage, int* warps, int* n_sm, cudaStream_t* st);
 // The problem's device descriptor (an array of one).
 const DevProblem* problem_device(const ::dmr_problem* p);
+// The CUDA device the problem was created on (-1 for a null problem).
+int problem_device_id(const ::dmr_problem* p);
 
 }  // namespace dmr

@@ -4,11 +4,11 @@
 // library holds on every device that loads it, until the process exits.
 //
 // Who needs it: callers that must not call cudaMalloc/cudaFree at the point
-// of evaluation -- code that runs while a stream is being captured into a
-// CUDA graph (allocation is not permitted during capture), latency-critical
-// optimiser loops (cudaMalloc/cudaFree synchronise the device), and hosts
-// whose device memory is fully reserved by another allocator (a framework's
-// caching allocator that owns the whole budget).
+// of evaluation -- latency-critical optimiser loops (cudaMalloc/cudaFree
+// synchronise the device and can stall for milliseconds), and hosts whose
+// device memory is fully reserved by another allocator (a framework's caching
+// allocator that owns the whole budget, or a memory pool sized up front), so
+// that a library-side cudaMalloc would fail or evict the caller's data.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -79,6 +79,11 @@ extern "C" int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return err(DMR_ECUDA, "dmr_eval_one_noalloc: no current device");
+  // the scratch address is per device: the problem's kernels run on the
+  // problem's device, so that device must be the current one
+  if (problem_device_id(p) != dev)
+    return err(DMR_EINVAL, "dmr_eval_one_noalloc: the problem was created on device " +
+                               std::to_string(problem_device_id(p)) + ", the current device is " + std::to_string(dev));
   cudaPointerAttributes a1, a2;
   if (cudaPointerGetAttributes(&a1, coords) != cudaSuccess || cudaPointerGetAttributes(&a2, obj_out) != cudaSuccess ||
       (a1.type != cudaMemoryTypeDevice && a1.type != cudaMemoryTypeManaged) ||

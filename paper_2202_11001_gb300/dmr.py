@@ -410,9 +410,24 @@ class Problem:
 
     def eval_one_noalloc(self, coords, out):
         """Objectives of one candidate (device tensor [2, 3, P]) into ``out``
-        (device tensor [4]) without any allocation in the library."""
-        a = _Arg(coords, np.float64)
-        _check(self._lib.dmr_eval_one_noalloc(self.h, a.ptr, _addr(out)))
+        (device tensor [4]) without any allocation in the library.  Both must
+        already be contiguous float64 CUDA tensors of those sizes on the
+        current device: this method converts nothing, since a converted copy
+        would itself be an allocation (and could be freed before the queued
+        kernels read it)."""
+        import torch
+
+        dev = torch.cuda.current_device()
+        for name, t, n in (("coords", coords, 6 * self.P), ("out", out, 4)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise DmrError("eval_one_noalloc: %s must be a contiguous float64 CUDA tensor" % name)
+            if t.device.index != dev:
+                raise DmrError("eval_one_noalloc: %s is on cuda:%d, the current device is cuda:%d"
+                               % (name, t.device.index, dev))
+            if (t.numel() != n) if name == "coords" else (t.numel() < n):
+                raise DmrError("eval_one_noalloc: %s holds %d values, needs %s%d" % (
+                    name, t.numel(), "" if name == "coords" else "at least ", n))
+        _check(self._lib.dmr_eval_one_noalloc(self.h, coords.data_ptr(), out.data_ptr()))
         return out
 
     def samples(self, reset=False):

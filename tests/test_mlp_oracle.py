@@ -55,3 +55,50 @@ def test_gelu_closed_form():
     h = 1e-6
     zz = np.array([-3.0, -1.0, 0.0, 0.5, 2.0])
     assert np.allclose(mlp.gelu_grad(zz), (mlp.gelu(zz + h) - mlp.gelu(zz - h)) / (2 * h), atol=1e-8)
+
+
+def test_round_bf16_definition():
+    """BF16 rounding (8 significant bits, ties to even) against torch's own
+    float32 -> bfloat16 conversion, plus hand-checked ties."""
+    import torch
+
+    rng = np.random.default_rng(2)
+    x = np.concatenate([rng.normal(0, 1, 4000), rng.normal(0, 1e-3, 2000), rng.normal(0, 50, 2000)])
+    x32 = x.astype(np.float32)
+    want = torch.from_numpy(x32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.round_bf16(x32.astype(np.float64)), want)
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: ties go to the even
+    # significand (1); 1 + 3 * 2^-8 between 1 + 2^-7 and 1 + 2^-6 goes up
+    assert mlp.round_bf16(np.array([1 + 2.0 ** -8]))[0] == 1.0
+    assert mlp.round_bf16(np.array([1 + 3 * 2.0 ** -8]))[0] == 1 + 2.0 ** -6
+    assert mlp.round_bf16(np.array([-(1 + 3 * 2.0 ** -8)]))[0] == -(1 + 2.0 ** -6)
+    assert mlp.round_bf16(np.array([0.0, 1.5, -0.375]))[:].tolist() == [0.0, 1.5, -0.375]
+
+
+def test_bf16_operand_mode():
+    """BF16-operand mode: the forward pass stays within the BF16 bound of the
+    FP64 one, every gradient entry is bounded by its magnitude sum
+    (|sum a b| <= sum |a| |b|), and the mode changes nothing when every
+    operand is already BF16 and the hidden activations are rounded away
+    (a network of zero hidden weights)."""
+    rng = np.random.default_rng(3)
+    p = _params(rng, 0.1)
+    X = rng.normal(0, 1, (33, mlp.IN))
+    Y = rng.normal(0, 1, (33, 3))
+    o64, _ = mlp.forward(p, X)
+    o16, _ = mlp.forward(p, X, bf16_operands=True)
+    assert np.linalg.norm(o16 - o64) < 2.0 ** -6 * np.linalg.norm(o64)
+    g, mag = mlp.grad(p, X, Y, bf16_operands=True, magnitudes=True)
+    assert np.all(np.abs(g) <= mag * (1 + 1e-12) + 1e-300)
+    g64 = mlp.grad(p, X, Y)
+    assert np.linalg.norm(g - g64) < 2.0 ** -5 * np.linalg.norm(g64)
+    # zero hidden and output weights: every output is the output bias, for
+    # either mode; the first-layer gradient is then 0 in both
+    d = mlp.unpack(p)
+    for k in ("W2", "W3", "W4"):
+        d[k][:] = 0.0
+    d["b4"][: mlp.OUT] = mlp.round_bf16(rng.normal(0, 1, mlp.OUT))
+    pz = mlp.pack(d)
+    a, _ = mlp.forward(pz, X, bf16_operands=True)
+    assert np.array_equal(a, np.broadcast_to(d["b4"][: mlp.OUT], a.shape))
+    assert not np.any(mlp.unpack(mlp.grad(pz, X, Y, bf16_operands=True))["W1"])
