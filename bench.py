@@ -8,8 +8,16 @@ touched tetrahedra of every (group, candidate) trial, accept-if-improves and
 commit -- one CUDA-graph launch.  One voxel-sample is one (candidate,
 direction, voxel) squared-difference term.
 
-Default workload: 64^3 float32 ellipsoid pair, 5^3-point meshes (384 tets),
-20 guidance pairs, population 128, 125 single-point FOS groups.
+Default workload (batch64): 64 independent registration problems of uneven
+size (edge 32..128 voxels, meshes 4^3..9^3 points, populations 64..512),
+one generation of single-point FOS partial evaluations over all of them per
+step, one CUDA graph.  Secondary workloads: --workload ellipsoid64 | ct |
+ct_coarse | sphere16 (single problems), learned, mlp_forward, cube_multires.
+
+Besides the counted samples the line reports the samples the raster kernels
+actually mapped and sampled (executed); the rest were settled exactly without
+sampling (rows of 0 against an all-0 partner region), and the roofline
+fraction is taken on the executed ones.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,9 +47,9 @@ UNIT = "voxel-samples/s"
 ALG_OPS_PER_SAMPLE = 37
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one fast raster-pass launch (one wave of the
-# generation), from the ncu capture summarised in profiles/raster_fast_ellipsoid64.md;
-# None for workloads without a capture of the current kernel.
-FAST_PASS_DRAM_BYTES = {("ellipsoid64", "f32"): 75.46e6}
+# generation), from the ncu capture of the current kernel summarised under
+# profiles/, per (workload, storage); None for workloads without one.
+FAST_PASS_DRAM_BYTES = {}
 
 
 def reduce_over_ranks(total_s, samples, dist, device):
@@ -89,63 +97,285 @@ def workload(name, seed):
     return pr
 
 
-def run_batch(args):
-    """--workload batch64: 64 independent problems (edge 32..128 voxels, 4..9
-    mesh points per axis, population 64..512) in one graph per generation."""
-    import torch
+BATCH_DESC = ("batch64: 64 independent problems built like the mid ellipsoid configuration (edge U{32..128} "
+              "voxels, meshes U{4..9}^3 points, populations U{64..512}, 8 guidance pairs each), one generation of "
+              "single-point FOS partial evaluations, one persistent launch per kernel and wave, one CUDA graph "
+              "per generation")
 
-    from paper_2202_11001_gb300 import dmr, synth
 
-    probs = synth.batch_problems(seed=2)
-    stream = torch.cuda.current_stream().cuda_stream
-    gs, cands, dels = [], [], []
+def batch_inputs(seed, n_problems=0):
+    """The 64 seeded problems, their FOS groups and per-problem proposal
+    offsets of one generation."""
+    from paper_2202_11001_gb300 import synth
+
+    probs = synth.batch_problems(seed=seed)
+    if n_problems:
+        probs = probs[:n_problems]
+    groups, dels = [], []
     for i, pr in enumerate(probs):
         C = pr["coords"].shape[0]
         pr["sigma"] = 0.1 * pr["img"][0].shape[0] / (pr["mesh"][0] - 1)
+        gr = synth.single_point_fos(pr["mesh"])
+        groups.append(gr)
+        dels.append(deltas_for(pr, gr, C, np.random.default_rng(500 + i)))
+    return probs, groups, dels
+
+
+def build_batch(probs, groups, storage, stream):
+    import torch
+
+    from paper_2202_11001_gb300 import dmr
+
+    gs = []
+    for pr, gr in zip(probs, groups):
+        C = pr["coords"].shape[0]
         g = dmr.Problem(pr["img"][0], pr["img"][1], *pr["spacing"], pr["mesh"], guide=pr["guide"],
-                        model=dmr.LINEAR, storage=args.storage, max_candidates=C, stream=stream)
+                        model=dmr.LINEAR, storage=storage, max_candidates=C, stream=stream)
         g.eval_full(torch.from_numpy(pr["coords"]).cuda())
-        groups = synth.single_point_fos(pr["mesh"])
-        g.set_fos(groups)
+        g.set_fos(gr)
         gs.append(g)
-        cands.append(np.arange(C, dtype=np.int32))
-        dels.append(deltas_for(pr, groups, C, np.random.default_rng(500 + i)))
-    big = max(range(len(gs)), key=lambda i: probs[i]["coords"].shape[0] * gs[i].ntet)
-    w, v, table = gs[big].autotune()
+    return gs
+
+
+def batch_tile(gs, probs, tile):
+    """The raster tile of a batch plan: fixed (--tile) or autotuned on the
+    problem with the most work; plans take the first problem's tile."""
+    if tile:
+        w, v = (int(x) for x in tile.lower().split("x"))
+        table = {}
+    else:
+        big = max(range(len(gs)), key=lambda i: probs[i]["coords"].shape[0] * gs[i].ntet)
+        w, v, table = gs[big].autotune()
     gs[0].set_tile(w, v)
+    return w, v, table
+
+
+def time_plan(plan, steps, flush, ev0, ev1):
+    """Device time of `steps` plan runs (L2 flushed before each, outside the
+    event bracket): per-step ms and summed raster-kernel ms."""
+    import torch
+
+    step_ms, raster_ms = [], 0.0
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record()
+        plan.run()
+        ev1.record()
+        torch.cuda.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        raster_ms += plan.kernel_ms()[1]
+    return step_ms, raster_ms
+
+
+def batch_counts(gs):
+    c = e = 0
+    for g in gs:
+        a, b = g.sample_counts(reset=True)
+        c += a
+        e += b
+    return c, e
+
+
+def cpu_baseline_batch(probs, groups, min_s=10.0, max_s=30.0, n_probs=4, n_cand=16):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the batch workload: for n_probs problems spread over the batch, one wave of
+    partial evaluations of its first n_cand candidates, cycled until about
+    min_s of oracle time; samples = the oracle's own coverage counts."""
+    from oracle import oracle as orc
+    from paper_2202_11001_gb300 import synth
+
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    pick = [int(round(k * (len(probs) - 1) / max(1, n_probs - 1))) for k in range(n_probs)]
+    work = []
+    rng = np.random.default_rng(7)
+    for q in pick:
+        pr, gr = probs[q], groups[q]
+        o = orc.Oracle(pr["img"][0], pr["img"][1], *pr["spacing"], pr["mesh"], guide=pr["guide"],
+                       model=orc.LINEAR)
+        nc = min(n_cand, pr["coords"].shape[0])
+        o.eval_full(pr["coords"][:nc])
+        m = pr["mesh"]
+        # a wave of independent groups: points of one coordinate parity class
+        w = np.array([g for g in range(len(gr)) if (g % m[0]) % 2 == 0 and ((g // m[0]) % m[1]) % 2 == 0
+                      and (g // (m[0] * m[1])) % 2 == 0])
+        gids = np.repeat(w, nc)
+        cids = np.tile(np.arange(nc), len(w))
+        cur = np.stack([o.coords(c) for c in range(nc)])
+        tc = synth.trial_coords(cur, gr, gids, cids, pr["sigma"], m, rng)
+        work.append((o, gr, gids, cids, tc))
+    samples, secs, it, ntr = 0, 0.0, 0, 0
+    cov = []
+    while secs < min_s and secs < max_s:
+        o, gr, gids, cids, tc = work[it % len(work)]
+        t0 = time.perf_counter()
+        o.eval_partial(gr, gids, cids, tc)
+        secs += time.perf_counter() - t0
+        if it < len(work):
+            cov.append(sum(int(o.trial(k, cap=256)["cov"].sum()) for k in range(len(gids))))
+        samples += cov[it % len(work)]
+        ntr += len(gids)
+        it += 1
+    return {"value": samples / secs, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
+            "sample": "%d wave evaluations over problems %s of the batch (one wave of single-point groups x the "
+                      "first %d candidates each, cycled; %d trials, %d voxel-samples), FP64 C oracle, OpenMP over "
+                      "trials, %.1f s" % (it, pick, n_cand, ntr, samples, secs)}
+
+
+def run_batch(args):
+    """--workload batch64 (the default): 64 independent problems of uneven
+    size, one CUDA-graph generation over all of them per step."""
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2202_11001_gb300 import dmr
+
+    # every replica its own seeded batch (independent populations, no exchange)
+    probs, groups, dels = batch_inputs(2 + rank, args.problems)
+    stream = torch.cuda.current_stream().cuda_stream
+    cands = [np.arange(pr["coords"].shape[0], dtype=np.int32) for pr in probs]
+    gs = build_batch(probs, groups, args.storage, stream)
+    w, v, table = batch_tile(gs, probs, args.tile)
     bt = dmr.Batch(gs)
     plan = bt.plan_generation(cands, dels)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.warmup):
         plan.run()
     torch.cuda.synchronize()
-    for g in gs:
-        g.samples(reset=True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms, ra = [], 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0.record()
+    batch_counts(gs)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, raster_ms = time_plan(plan, args.steps, flush, ev0, ev1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    counted, executed = batch_counts(gs)
+    total_s = sum(step_ms) / 1e3
+    total_s, all_samples = reduce_over_ranks(total_s, counted, dist, "cuda")
+    value = all_samples / total_s
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+
+    # e2e through the public API with host buffers: every step uploads each
+    # problem's proposal offsets from pinned host memory into the plan
+    # (dmr_plan_update), runs it (dmr_plan_run) and reads every problem's
+    # objectives back (dmr_objectives_out)
+    e2e = None
+    if args.e2e_steps > 0:
+        pins = [torch.from_numpy(np.ascontiguousarray(d)).pin_memory() for d in dels]
+        plan.update(pins)
         plan.run()
-        e1.record()
+        for g in gs:
+            g.objectives()
         torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        ra += plan.kernel_ms()[1]
-    samples = sum(g.samples(reset=True) for g in gs)
-    tot = sum(ms) / 1e3
-    line = {"metric": METRIC, "value": samples / tot, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
-            "data": "synthetic (64 seeded ellipsoid problems)",
-            "config": {"workload": "batch64: 64 problems, edge U{32..128}, mesh U{4..9}^3 points, population "
-                                   "U{64..512}, one persistent launch per kernel and wave, one graph per generation",
-                       "storage": args.storage, "problems": len(gs), "tile": [w, v],
-                       "samples_per_step": samples / args.steps,
-                       "raster_ms_per_step": ra / args.steps},
-            "gpu_launches": plan.launches * args.steps}
-    print(json.dumps(line), flush=True)
+        batch_counts(gs)
+        d2h = 0
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.update(pins)
+            plan.run()
+            d2h = 0
+            for g in gs:
+                d2h += g.objectives().nbytes
+        dt = time.perf_counter() - t0
+        ec, _ = batch_counts(gs)
+        e2e = {"value": ec / dt, "unit": UNIT, "h2d_bytes_per_step": int(sum(p.numel() * 8 for p in pins)),
+               "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+               "path": "dmr_plan_update (pinned host offsets of all 64 problems) + dmr_plan_run + "
+                       "dmr_objectives_out per problem, per generation"}
+
+    peaks, peak_kind = measured_peaks()
+    clock_max = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = n_sm * 128 * clock_max * 1e6 / 1e12
+    raster_s = raster_ms / 1e3 / args.steps
+    counted_step, executed_step = counted / args.steps, executed / args.steps
+    bpv = 4 if args.storage == "f32" else 2
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    achieved = executed_step * ALG_OPS_PER_SAMPLE / raster_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-op/s",
+                "frac": achieved / alu_peak, "traffic": FAST_PASS_DRAM_BYTES.get(("batch64", args.storage)),
+                "traffic_unit": "DRAM bytes per fast raster-pass launch (one wave), ncu",
+                "kernel": "k_raster (rasterise + map + trilinear sample + SSD), fast and full-logic passes",
+                "ops_per_sample": ALG_OPS_PER_SAMPLE, "basis": "executed samples",
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clock_max),
+                "raster_ms_per_step": raster_s * 1e3,
+                "counted_samples_per_step": counted_step, "executed_samples_per_step": executed_step,
+                "executed_frac": executed_step / max(counted_step, 1.0),
+                "executed_samples_per_s_raster": executed_step / raster_s,
+                "touched_bytes_frac_of_hbm": value * 2 * bpv / 1e9 / hbm,
+                "touched_bytes_frac_of_hbm_executed": executed_step / (total_s / args.steps) * 2 * bpv / 1e9 / hbm,
+                "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind}
+    launches = plan.launches
     plan.close()
     bt.close()
+
+    variants = {}
+    if not args.no_variants and world == 1:
+        for st in ("f32", "bf16", "f16"):
+            if st == args.storage:
+                variants[st] = {"value": value, "executed_per_s": executed / (sum(step_ms) / 1e3)}
+                continue
+            gv = build_batch(probs, groups, st, stream)
+            batch_tile(gv, probs, args.tile)
+            bv = dmr.Batch(gv)
+            pv = bv.plan_generation(cands, dels)
+            for _ in range(3):
+                pv.run()
+            torch.cuda.synchronize()
+            batch_counts(gv)
+            ms, _ = time_plan(pv, max(3, args.steps // 2), flush, ev0, ev1)
+            c, e = batch_counts(gv)
+            variants[st] = {"value": c / (sum(ms) / 1e3), "executed_per_s": e / (sum(ms) / 1e3)}
+            pv.close()
+            bv.close()
+            for g in gv:
+                g.close()
+
+    precision = None
+    if not args.no_variants and rank == 0 and world == 1:
+        # the first problem of the batch with an edge of at most 64 voxels
+        q = next(i for i, pr in enumerate(probs) if pr["img"][0].shape[0] <= 64)
+        precision = precision_report(probs[q], stream)
+        precision["problem"] = probs[q]["name"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_batch(probs, groups)
+
+    for g in gs:
+        g.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+                "data": "synthetic (64 seeded ellipsoid problems per replica)",
+                "config": {"workload": BATCH_DESC, "storage": args.storage, "problems": len(probs),
+                           "population_total": int(sum(len(c) for c in cands)),
+                           "samples_per_step": counted_step, "executed_samples_per_step": executed_step,
+                           "tile": {"warps_per_cta": w, "voxels_per_warp": v,
+                                    "autotune_ms": {"%dx%d" % k: round(t, 4) for k, t in table.items()}},
+                           "l2": "flushed before every timed step (256 MiB write outside the event bracket)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches * args.steps, "variants_samples_per_s": variants,
+                "precision": precision}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -465,36 +695,59 @@ def precision_report(pr, stream, n_cand=8):
     return out
 
 
+def _parity_waves(m, n_groups):
+    """Waves of independent single-point groups: points of equal coordinate
+    parity have disjoint stars."""
+    par = [((p % m[0]) & 1) + 2 * (((p // m[0]) % m[1]) & 1) + 4 * ((p // (m[0] * m[1])) & 1)
+           for p in range(n_groups)]
+    return [np.array([g for g in range(n_groups) if par[g] == c]) for c in range(8)]
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle, timed on the host cores, on bounded
-    samples of the same workload (one wave of the generation per step)."""
+    samples of the same workload.  batch64: each step is one wave of partial
+    evaluations of 8 candidates of one of 4 problems spread over the batch
+    (cycled); single problems: one wave of a quarter of the population."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from oracle import oracle as orc
     from paper_2202_11001_gb300 import synth
 
-    pr = workload(args.workload, 0)
-    C = pr["coords"].shape[0]
-    groups = synth.single_point_fos(pr["mesh"])
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    src, tgt = pr["img"]
-    o = orc.Oracle(src, tgt, *pr["spacing"], pr["mesh"], guide=pr["guide"], model=orc.LINEAR)
-    o.eval_full(pr["coords"])
-    # waves of independent groups: points with equal coordinate parity
-    m = pr["mesh"]
-    par = [((p % m[0]) & 1) + 2 * (((p // m[0]) % m[1]) & 1) + 4 * ((p // (m[0] * m[1])) & 1) for p in range(len(groups))]
-    waves = [np.array([g for g in range(len(groups)) if par[g] == c]) for c in range(8)]
-    ncand = max(8, C // 4)
+    units = []  # (oracle, groups, waves, candidates, sigma, mesh)
+    if args.workload == "batch64":
+        probs, groups, _ = batch_inputs(2)
+        pick = [0, 21, 42, 63]
+        ncand = 8
+        for q in pick:
+            pr = probs[q]
+            o = orc.Oracle(pr["img"][0], pr["img"][1], *pr["spacing"], pr["mesh"], guide=pr["guide"],
+                           model=orc.LINEAR)
+            o.eval_full(pr["coords"][:ncand])
+            units.append((o, groups[q], _parity_waves(pr["mesh"], len(groups[q])), pr["sigma"], pr["mesh"]))
+        desc = BATCH_DESC
+        step_desc = "one wave of partial evaluations of %d candidates of one of problems %s (cycled)" % (ncand, pick)
+    else:
+        pr = workload(args.workload, 0)
+        C = pr["coords"].shape[0]
+        groups = synth.single_point_fos(pr["mesh"])
+        o = orc.Oracle(pr["img"][0], pr["img"][1], *pr["spacing"], pr["mesh"], guide=pr["guide"], model=orc.LINEAR)
+        o.eval_full(pr["coords"])
+        ncand = max(8, C // 4)
+        units.append((o, groups, _parity_waves(pr["mesh"], len(groups)), pr["sigma"], pr["mesh"]))
+        desc = pr["desc"]
+        step_desc = "one wave of partial evaluations for %d candidates (bounded sample)" % ncand
     rng = np.random.default_rng(11)
     tot_s, tot_n = 0.0, 0
     for step in range(args.warmup + args.steps):
-        w = waves[step % 8]
+        o, groups, waves, sigma, m = units[step % len(units)]
+        w = waves[(step // len(units)) % 8]
         gids = np.repeat(w, ncand)
         cids = np.tile(np.arange(ncand), len(w))
         cur = np.stack([o.coords(c) for c in range(ncand)])
-        tc = synth.trial_coords(cur, groups, gids, cids, pr["sigma"], pr["mesh"], rng)
+        tc = synth.trial_coords(cur, groups, gids, cids, sigma, m, rng)
         t0 = time.perf_counter()
         o.eval_partial(groups, gids, cids, tc)
         dt = time.perf_counter() - t0
@@ -506,10 +759,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": pr["desc"], "step": "one wave of partial evaluations for "
-                                                                     "%d candidates (bounded sample)" % ncand},
+            "data": "synthetic", "config": {"workload": desc, "step": step_desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": orc.max_threads(),
-                             "sample": "one wave x %d candidates per step" % ncand},
+                             "sample": step_desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -521,13 +773,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ellipsoid64")
+    ap.add_argument("--workload", default="batch64")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--generations", default="300,600", help="cube_multires: generations per level")
     ap.add_argument("--tile", default="", help="fixed raster tile WARPSxVOXELS (e.g. 4x32) instead of autotuning")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="batch64: only the first N problems (small profiling captures; not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3")
@@ -587,7 +841,7 @@ def main():
     for _ in range(args.warmup):
         plan.run()
     torch.cuda.synchronize()
-    g.samples(reset=True)
+    g.sample_counts(reset=True)
     sampler = ClockSampler(local)
     sampler.start()
     step_ms, raster_ms = [], 0.0
@@ -608,7 +862,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    samples = g.samples(reset=True)
+    samples, executed = g.sample_counts(reset=True)
     total_s = sum(step_ms) / 1e3
     total_s, all_samples = reduce_over_ranks(total_s, samples, dist, "cuda")
     value = all_samples / total_s
@@ -669,7 +923,8 @@ def main():
     clock_max = clocks.get("sm_max_mhz") or 2070.0
     alu_peak = n_sm * 128 * clock_max * 1e6 / 1e12  # T lane-ops/s
     raster_s_per_step = raster_ms / 1e3 / args.steps
-    achieved = samples_per_step * ALG_OPS_PER_SAMPLE / raster_s_per_step / 1e12
+    executed_per_step = executed / args.steps
+    achieved = executed_per_step * ALG_OPS_PER_SAMPLE / raster_s_per_step / 1e12
     bpv = 4 if args.storage == "f32" else 2
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     traffic = FAST_PASS_DRAM_BYTES.get((args.workload, args.storage))
@@ -677,9 +932,11 @@ def main():
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per fast raster-pass launch (one wave), ncu",
                 "kernel": "k_raster (rasterise + map + trilinear sample + SSD)",
-                "ops_per_sample": ALG_OPS_PER_SAMPLE,
+                "ops_per_sample": ALG_OPS_PER_SAMPLE, "basis": "executed samples",
                 "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clock_max),
                 "raster_ms_per_step": raster_s_per_step * 1e3,
+                "counted_samples_per_step": samples_per_step, "executed_samples_per_step": executed_per_step,
+                "executed_frac": executed_per_step / max(samples_per_step, 1.0),
                 "touched_bytes_frac_of_hbm": value * 2 * bpv / 1e9 / hbm,
                 "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind}
 
@@ -724,6 +981,7 @@ def main():
                 "config": {"workload": pr["desc"], "storage": args.storage, "population": C,
                            "fos_groups": len(groups), "waves": len(waves), "mesh_pts": list(pr["mesh"]),
                            "deform_model": "linear_elastic", "samples_per_step": samples_per_step,
+                           "executed_samples_per_step": executed_per_step,
                            "tile": {"warps_per_cta": tile_w, "voxels_per_warp": tile_v,
                                     "autotune_ms": {"%dx%d" % k: round(v, 4) for k, v in tile_table.items()}},
                            "l2": "flushed before every timed step (256 MiB write outside the event bracket)",

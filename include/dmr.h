@@ -163,9 +163,19 @@ int dmr_landmarks_out(dmr_problem* p, int cand, int* loc, double* term);
  * new coverage [n][2], ssd [n][2], def [n], fold [n].  Returns the touched
  * count (>= 0) or a negative status; outputs may be NULL. */
 int dmr_trial_out(dmr_problem* p, int k, int* tets, int* cov, double* ssd, double* def, int* fold);
-/* Voxel-samples (one per covered voxel per direction) evaluated by the
- * device since the last reset; reset != 0 zeroes the counter after reading. */
+/* Voxel-samples (one per covered voxel per direction, Sec. 2.3.1) evaluated
+ * by the device since the last reset; reset != 0 zeroes both counters of
+ * dmr_sample_counts after reading. */
 int dmr_samples(dmr_problem* p, long long* samples, int reset);
+/* Both sample counters since the last reset: *counted as dmr_samples, and
+ * *executed = the samples the rasterise-and-sample kernels actually mapped
+ * through the affine map and sampled from the partner image.  The rest were
+ * settled without sampling: a row of voxels that are 0 whose every sample
+ * can reach only partner voxels that are 0 adds exactly 0 (black against
+ * black, or 0 - 0), and an item whose reachable partner region is all 0
+ * reads only its own voxels.  Either pointer (host) may be NULL, not both;
+ * reset != 0 zeroes both after reading. */
+int dmr_sample_counts(dmr_problem* p, long long* counted, long long* executed, int reset);
 
 /* Generation plan (batched partial evaluation captured in one CUDA graph):
  * for every wave of the FOS in order, for every candidate in cand_ids:

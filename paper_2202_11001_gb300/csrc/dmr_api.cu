@@ -181,6 +181,7 @@ struct dmr_problem {
   uint8_t* cflag[2] = {nullptr, nullptr};
   unsigned long long* cmask[2] = {nullptr, nullptr};
   int* nzsat[2] = {nullptr, nullptr};
+  unsigned long long* occ[2] = {nullptr, nullptr};
   int4* d_tet = nullptr;
   uint32_t* d_fperm = nullptr;
   uint8_t* d_fix = nullptr;
@@ -351,6 +352,7 @@ void release_problem(dmr_problem* p) {
     dfree(p->cflag[k]);
     dfree(p->cmask[k]);
     dfree(p->nzsat[k]);
+    dfree(p->occ[k]);
   }
   dfree(p->d_tet); dfree(p->d_fperm); dfree(p->d_fix); dfree(p->d_restvol); dfree(p->d_guide);
   dfree(p->d_star_ptr); dfree(p->d_star);
@@ -481,8 +483,9 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       // nonzero counts fit an int below 2^31 voxels; larger images go without
       const long ns = (long)(p->n[k][0] + 1) * (p->n[k][1] + 1) * (p->n[k][2] + 1);
       if (nv < (1L << 31)) {
-        if ((rc = dalloc(&p->nzsat[k], ns))) goto fail_;
+        if ((rc = dalloc(&p->nzsat[k], ns)) || (rc = dalloc(&p->occ[k], occ_words(p->n[k])))) goto fail_;
         launch_build_nzsat(p->plain[k], p->storage, p->n[k], p->nzsat[k], p->st);
+        launch_build_occ(p->plain[k], p->storage, p->n[k], p->occ[k], p->st);
       }
     }
     if (tmp) {
@@ -542,7 +545,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
         (rc = dalloc(&p->d_cov, C * p->ntet * 2)) || (rc = dalloc(&p->d_def, C * p->ntet)) ||
         (rc = dalloc(&p->d_fold, C * p->ntet)) || (rc = dalloc(&p->d_loc, C * 2 * std::max(1, p->ng))) ||
         (rc = dalloc(&p->d_gterm, C * 2 * std::max(1, p->ng))) || (rc = dalloc(&p->d_sums, C * 4)) ||
-        (rc = dalloc(&p->d_samples, 1)) || (rc = dalloc(&p->d_prob, 1)) || (rc = dalloc(&p->d_obj, C * 4)))
+        (rc = dalloc(&p->d_samples, 2)) || (rc = dalloc(&p->d_prob, 1)) || (rc = dalloc(&p->d_obj, C * 4)))
       goto fail_;
     if (!p->gs_id.empty()) {
       if ((rc = dalloc(&p->d_gs_id, p->gs_id.size())) || (rc = dalloc(&p->d_gs_ptr, p->gs_ptr.size())) ||
@@ -558,7 +561,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
     cudaMemcpyAsync(p->d_restvol, rv.data(), sizeof(float) * p->ntet, cudaMemcpyHostToDevice, p->st);
     if (p->ng)
       cudaMemcpyAsync(p->d_guide, p->guide.data(), sizeof(double) * p->guide.size(), cudaMemcpyHostToDevice, p->st);
-    cudaMemsetAsync(p->d_samples, 0, sizeof(unsigned long long), p->st);
+    cudaMemsetAsync(p->d_samples, 0, 2 * sizeof(unsigned long long), p->st);
     DevProblem& h = p->hp;
     memset(&h, 0, sizeof(h));
     for (int k = 0; k < 2; ++k) {
@@ -567,6 +570,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       h.cflag[k] = p->cflag[k];
       h.cmask[k] = p->cmask[k];
       h.nzsat[k] = p->nzsat[k];
+      h.occ[k] = p->occ[k];
       for (int a = 0; a < 3; ++a) {
         h.n[k][a] = p->n[k][a];
         h.spd[k][a] = p->sp[k][a];
@@ -605,6 +609,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
     h.c_gterm = p->d_gterm;
     h.sums = p->d_sums;
     h.samples = p->d_samples;
+    h.executed = p->d_samples + 1;
     if ((rc = upload_prob(p))) goto fail_;
     cudaError_t e = cudaStreamSynchronize(p->st);
     if (e != cudaSuccess) {
@@ -1212,15 +1217,18 @@ int dmr_refine(const double* coarse, int n_cand, const int* m, double* fine, voi
   return DMR_OK;
 }
 
-int dmr_samples(dmr_problem* p, long long* samples, int reset) {
-  if (!p || !samples) return fail(DMR_EINVAL, "null argument");
-  unsigned long long v = 0;
-  CU(cudaMemcpyAsync(&v, p->d_samples, sizeof(v), cudaMemcpyDeviceToHost, p->st));
+int dmr_sample_counts(dmr_problem* p, long long* counted, long long* executed, int reset) {
+  if (!p || (!counted && !executed)) return fail(DMR_EINVAL, "null argument");
+  unsigned long long v[2] = {0, 0};
+  CU(cudaMemcpyAsync(v, p->d_samples, sizeof(v), cudaMemcpyDeviceToHost, p->st));
   CU(cudaStreamSynchronize(p->st));
-  *samples = (long long)v;
+  if (counted) *counted = (long long)v[0];
+  if (executed) *executed = (long long)v[1];
   if (reset) CU(cudaMemsetAsync(p->d_samples, 0, sizeof(v), p->st));
   return DMR_OK;
 }
+
+int dmr_samples(dmr_problem* p, long long* samples, int reset) { return dmr_sample_counts(p, samples, nullptr, reset); }
 
 // ------------------------------------------------------------ autotuner
 int dmr_autotune(dmr_problem* p, int n_cand, int* best_warps, int* best_vpw, float* ms_table) {

@@ -412,12 +412,38 @@ static __device__ __noinline__ bool black_exact(const ItemRec& r, const DevProbl
 }
 
 
+// True when every 4x4x4 voxel block that meets the box [x0, x1] x [y0, y1] x
+// [z0, z1] (inclusive, inside the image of dimensions nx, ny) holds only 0s,
+// from the image's block occupancy bitmap (DevProblem::occ).
+static __device__ __forceinline__ bool occ_box_zero(const unsigned long long* __restrict__ occ, int nx, int ny,
+                                                    int x0, int y0, int z0, int x1, int y1, int z1) {
+  const int BY = (ny + 3) >> 2, W = (((nx + 3) >> 2) + 63) >> 6;
+  const int bx0 = x0 >> 2, bx1 = x1 >> 2, w0 = bx0 >> 6, w1 = bx1 >> 6;
+  for (int bz = z0 >> 2; bz <= (z1 >> 2); ++bz)
+    for (int by = y0 >> 2; by <= (y1 >> 2); ++by) {
+      const unsigned long long* row = occ + ((long)bz * BY + by) * W;
+      for (int w = w0; w <= w1; ++w) {
+        const int lo = w == w0 ? (bx0 & 63) : 0, hi = w == w1 ? (bx1 & 63) : 63;
+        if (__ldg(row + w) & (~0ull >> (63 - hi)) & (~0ull << lo)) return false;
+      }
+    }
+  return true;
+}
+
 // ------------------------------------------------------------ raster + sample
 struct WarpSmem {
   ItemRec rec;
   int2 meta[32];     // (exclusive voxel prefix, own plain index of x0) per row
   float4 pr0[32];    // mapped partner-relative coordinate of x0 per row
   int forder, fshape;  // fast pass: the item's faces sorted by the sign of A.x (face_order)
+  // empty-space test of the rows: own and partner block occupancy bitmaps,
+  // partner dimensions, mode (0 off, 1 own rows only: the partner region is
+  // all 0, 2 own rows and the partner region)
+  const unsigned long long* zown;
+  const unsigned long long* zpar;
+  int zn[3];
+  int zon;
+  unsigned execd;  // samples of the current item mapped and sampled so far
 };
 
 template <int ST>
@@ -587,9 +613,13 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
       for (int i = threadIdx.x; i < NW; i += 32 * WARPS) dst[i] = __ldg(src + i);
       __syncthreads();
     } else {
+      // the fast pass reads a record only up to its FP64 vertex copies (those
+      // serve the careful spans and the exact black decision of the
+      // full-logic pass), so it copies only those words
+      constexpr int NR = FAST ? (int)(offsetof(ItemRec, X) / 16) : NW;
       const int4* src = (const int4*)(b.rec + item);
       int4* dst = (int4*)&ws->rec;
-      for (int i = lane; i < NW; i += 32) dst[i] = __ldg(src + i);
+      for (int i = lane; i < NR; i += 32) dst[i] = __ldg(src + i);
       __syncwarp();
     }
     const ItemRec& r = rs->rec;
@@ -613,10 +643,26 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
       const int Ox = r.O[0], Oy = r.O[1], Oz = r.O[2];
       const int xl = r.b0[0] - Ox, xh = r.b1[0] - Ox;
       const int by0 = r.b0[1], by1 = r.b1[1];
-      if constexpr (FAST) {
-        if (lane == 0) face_order(r, ws->forder, ws->fshape);
-        __syncwarp();
+      // empty-space test per row: a row whose own voxels are all 0 and whose
+      // samples can reach only partner voxels that are 0 adds exactly 0
+      // (every sample is 0 and black: black against black, or 0 - 0), so it
+      // is counted but not sampled.  Needs a finite small map (bit5) and a
+      // partner region that is not known to hold no 0 (bit3);
+      // it reads the images' 4x4x4 block occupancy bitmaps (a few KB, cached
+      // on chip).  Its parameters wait in shared memory (read where used, so
+      // that they hold no registers across the loops).
+      if (lane == 0) {
+        if constexpr (FAST) face_order(r, ws->forder, ws->fshape);
+        const unsigned long long* zo = pr.occ[d];
+        const unsigned long long* zp = pr.occ[1 - d];
+        const bool on = zo != nullptr && zp != nullptr && (r.flags & 32) && !(r.flags & 8);
+        ws->zown = zo;
+        ws->zpar = zp;
+        ws->zon = on ? (pzero ? 1 : 2) : 0;
+        for (int a = 0; a < 3; ++a) ws->zn[a] = pr.n[1 - d][a];
+        ws->execd = 0u;
       }
+      __syncwarp();
       for (int zb = r.b0[2]; zb <= r.b1[2]; zb += 32) {
         const int z = zb + lane;
         int ycnt = 0, ylo = 0;
@@ -676,18 +722,59 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           if constexpr (FAST) {
             if (__any_sync(FULL_MASK, careful)) goto handover;
           }
+          // every voxel of the batch's rows is one sample (counted)
+          cov += __reduce_add_sync(FULL_MASK, (unsigned)xcnt);
           if ((*(volatile int*)&r.flags & 20) == 20) {
             // own and partner voxels all 0: every sample adds 0, only the
             // batch's voxel count matters
-            cov += __reduce_add_sync(FULL_MASK, (unsigned)xcnt);
             continue;
           }
-          const unsigned nzm = __ballot_sync(FULL_MASK, xcnt > 0);
+          int xs = xcnt;  // voxels of this row that are sampled
+          if (xcnt > 0 && *(volatile int*)&ws->zon) {
+            bool skip = occ_box_zero(*(const unsigned long long* volatile*)&ws->zown, nxo, nyo, x0, yrow, zrow,
+                                     x0 + xcnt - 1, yrow, zrow);
+            if (skip && *(volatile int*)&ws->zon == 2) {
+              // the samples' FP32 positions run from the row start p to
+              // p + (xcnt - 1) gx (the loop's own expressions, monotone in the
+              // step, clamps included); every exact support lies within 1 voxel
+              // below / 2 above the FP32 cell, clamped to the image
+              const float vx = (float)(x0 - Ox), vy = (float)(yrow - Oy), vz = (float)(zrow - Oz);
+              const float4 g0 = lds4(&r.G[0][0]), g1 = lds4(&r.G[1][0]), g2 = lds4(&r.G[2][0]);
+              const float4 gx = lds4(&r.gx[0]), lo = lds4(&r.clo[0]), hi = lds4(&r.chi[0]);
+              const float dl = (float)(xcnt - 1);
+              float ax = vx + fmaf(g0.x, vx, fmaf(g0.y, vy, fmaf(g0.z, vz, g0.w)));
+              float ay = vy + fmaf(g1.x, vx, fmaf(g1.y, vy, fmaf(g1.z, vz, g1.w)));
+              float az = vz + fmaf(g2.x, vx, fmaf(g2.y, vy, fmaf(g2.z, vz, g2.w)));
+              float qx = fmaf(dl, gx.x, ax), qy = fmaf(dl, gx.y, ay), qz = fmaf(dl, gx.z, az);
+              if (!(*(volatile int*)&r.flags & 2)) {
+                ax = fminf(fmaxf(ax, lo.x), hi.x);
+                ay = fminf(fmaxf(ay, lo.y), hi.y);
+                az = fminf(fmaxf(az, lo.z), hi.z);
+                qx = fminf(fmaxf(qx, lo.x), hi.x);
+                qy = fminf(fmaxf(qy, lo.y), hi.y);
+                qz = fminf(fmaxf(qz, lo.z), hi.z);
+              }
+              int zn[3];
+              for (int a = 0; a < 3; ++a) zn[a] = *(volatile int*)&ws->zn[a];
+              const int lx = max((int)floorf(fminf(ax, qx)) - 1 + *(volatile int*)&r.Op[0], 0);
+              const int ly = max((int)floorf(fminf(ay, qy)) - 1 + *(volatile int*)&r.Op[1], 0);
+              const int lz = max((int)floorf(fminf(az, qz)) - 1 + *(volatile int*)&r.Op[2], 0);
+              const int hx = min((int)floorf(fmaxf(ax, qx)) + 2 + *(volatile int*)&r.Op[0], zn[0] - 1);
+              const int hy = min((int)floorf(fmaxf(ay, qy)) + 2 + *(volatile int*)&r.Op[1], zn[1] - 1);
+              const int hz = min((int)floorf(fmaxf(az, qz)) + 2 + *(volatile int*)&r.Op[2], zn[2] - 1);
+              skip = lx > hx || ly > hy || lz > hz ||
+                     occ_box_zero(*(const unsigned long long* volatile*)&ws->zpar, zn[0], zn[1], lx, ly, lz, hx, hy,
+                                  hz);
+            }
+            if (skip) xs = 0;
+          }
+          const unsigned nzm = __ballot_sync(FULL_MASK, xs > 0);
           const int cidx = __popc(nzm & (lemask >> 1));
-          const int xincl = warp_incl_scan(xcnt, lane);
-          const int xexcl = xincl - xcnt;
+          const int xincl = warp_incl_scan(xs, lane);
+          const int xexcl = xincl - xs;
           const int T = __shfl_sync(FULL_MASK, xincl, 31);
-          if (xcnt > 0) {
+          if (T == 0) continue;
+          if (xs > 0) {
             const float vx = (float)(x0 - Ox), vy = (float)(yrow - Oy), vz = (float)(zrow - Oz);
             const float4 g0 = lds4(&r.G[0][0]), g1 = lds4(&r.G[1][0]), g2 = lds4(&r.G[2][0]);
             const float px = vx + fmaf(g0.x, vx, fmaf(g0.y, vy, fmaf(g0.z, vz, g0.w)));
@@ -704,6 +791,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           // partner tet well inside the image and a small map: mapped
           // coordinates cannot leave [-1, n], so the clamps are skipped
           const bool inside = (r.flags & 2) != 0;
+          if (lane == 0 && !pzero) ws->execd += (unsigned)T;
           int rows_before = 0;
           // plain FP32 partial sum over at most 256 voxels of the batch (<= 8
           // samples per lane), folded into the Kahan pair afterwards; the
@@ -722,7 +810,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
                 sum = tk;
                 bsum = 0.f;
               }
-              const unsigned bit = (xcnt > 0 && xexcl >= vb && xexcl < vb + 32) ? (1u << (xexcl - vb)) : 0u;
+              const unsigned bit = (xs > 0 && xexcl >= vb && xexcl < vb + 32) ? (1u << (xexcl - vb)) : 0u;
               const unsigned sm = __reduce_or_sync(FULL_MASK, bit);
               const int row = rows_before + __popc(sm & lemask) - 1;
               rows_before += __popc(sm);
@@ -745,7 +833,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
 #pragma unroll
             for (int u = 0; u < VPL; ++u) {
               const int wb = vb + 32 * u;
-              const unsigned bit = (xcnt > 0 && xexcl >= wb && xexcl < wb + 32) ? (1u << (xexcl - wb)) : 0u;
+              const unsigned bit = (xs > 0 && xexcl >= wb && xexcl < wb + 32) ? (1u << (xexcl - wb)) : 0u;
               const unsigned sm = __reduce_or_sync(FULL_MASK, bit);
               row[u] = rows_before + __popc(sm & lemask) - 1;
               rows_before += __popc(sm);
@@ -826,7 +914,6 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
             comp = (tk - sum) - yk;
             sum = tk;
           }
-          cov += T;  // every voxel of the batch's rows is one sample
           __syncwarp();
         }
       }
@@ -845,6 +932,8 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
         lo = lo + ol + err;
       }
       const int covt = __shfl_sync(FULL_MASK, cov, 0);  // cov is warp-uniform
+      if (lane == 0 && (rs->rec.flags & 1) && ws->execd)
+        atomicAdd(probs[rs->rec.prob].executed, (unsigned long long)ws->execd);
       if (!cta_mode) {
         if (lane == 0) {
           b.o_ssd[item] = (double)hi + (double)lo;

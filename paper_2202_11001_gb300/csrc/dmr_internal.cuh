@@ -31,6 +31,10 @@ struct DevProblem {
   // per image: count of nonzero voxels in [0, x) x [0, y) x [0, z), array
   // [(nz+1)][(ny+1)][(nx+1)] (NULL for images of 2^31 voxels or more)
   const int* nzsat[2];
+  // per image: occupancy of 4x4x4 voxel blocks, bit (bx & 63) of word
+  // (bz * BY + by) * W + (bx >> 6) set when block (bx, by, bz) holds a
+  // nonzero voxel; BX = ceil(nx / 4), BY = ceil(ny / 4), W = ceil(BX / 64)
+  const unsigned long long* occ[2];
   int n[2][3];
   double spd[2][3];
   float sp[2][3];
@@ -64,7 +68,8 @@ struct DevProblem {
   int* c_loc;               // [C][2][ng]
   double* c_gterm;          // [C][2][ng]
   double* sums;             // [C][4] raw sums
-  unsigned long long* samples;
+  unsigned long long* samples;   // voxel-samples evaluated (covered voxels of every evaluated tet)
+  unsigned long long* executed;  // of those, samples the raster kernels mapped and sampled
 };
 
 // Per (trial, tet, direction) set-up produced by the geometry kernel and
@@ -75,7 +80,8 @@ struct DevProblem {
 struct __align__(16) ItemRec {
   int flags;        // bit0: rasterise (6V_own > 0); bit1: clamp-free map; bit2 / bit3: every
                     // partner voxel a sample of this item can reach is 0 / is not 0; bit4 (with
-                    // bit2): the own voxels are 0 too
+                    // bit2): the own voxels are 0 too; bit5: the FP32 map is finite and small
+                    // (the rows' empty-space test may use it)
   int prob;
   int tet;
   int dir;
@@ -137,6 +143,10 @@ void launch_build_cells(const void* plain, int dtype, const int n[3], void* cell
 // Summed nonzero counts of an image (DevProblem::nzsat); sat holds
 // (nx+1)(ny+1)(nz+1) ints.
 void launch_build_nzsat(const void* plain, int dtype, const int n[3], int* sat, cudaStream_t st);
+// Block occupancy bitmap (DevProblem::occ); occ holds occ_words(n) words,
+// zeroed by the launch.
+long occ_words(const int n[3]);
+void launch_build_occ(const void* plain, int dtype, const int n[3], unsigned long long* occ, cudaStream_t st);
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
 void launch_refine(const double* coarse, int n_cand, const int m[3], double* fine, cudaStream_t st);
 void launch_link_check(const DevProblem* probs, const DevProblem& hp, const int* cands, int n_cand, int* out,

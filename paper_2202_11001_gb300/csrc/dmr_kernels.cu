@@ -152,6 +152,32 @@ void launch_build_nzsat(const void* plain, int dtype, const int n[3], int* sat, 
     k_nzsat_scan<<<(unsigned)((lines[a] + 127) / 128), 128, 0, st>>>(sat, X, Y, Z, a);
 }
 
+// Block occupancy: one thread per 4x4x4 block sets its bit when the block
+// holds a nonzero voxel.
+__global__ void k_occ(const void* plain, int st, int nx, int ny, int nz, unsigned long long* occ) {
+  const int BX = (nx + 3) >> 2, BY = (ny + 3) >> 2, BZ = (nz + 3) >> 2, W = (BX + 63) >> 6;
+  const long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (id >= (long)BX * BY * BZ) return;
+  const int bx = (int)(id % BX), by = (int)((id / BX) % BY), bz = (int)(id / ((long)BX * BY));
+  bool any = false;
+  for (int z = 4 * bz; z < min(4 * bz + 4, nz) && !any; ++z)
+    for (int y = 4 * by; y < min(4 * by + 4, ny) && !any; ++y)
+      for (int x = 4 * bx; x < min(4 * bx + 4, nx) && !any; ++x)
+        any = load_plain_dyn(plain, st, ((long)z * ny + y) * nx + x) != 0.0f;
+  if (any) atomicOr(occ + ((long)bz * BY + by) * W + (bx >> 6), 1ull << (bx & 63));
+}
+
+long occ_words(const int n[3]) {
+  const long BX = (n[0] + 3) >> 2, BY = (n[1] + 3) >> 2, BZ = (n[2] + 3) >> 2;
+  return BY * BZ * ((BX + 63) >> 6);
+}
+
+void launch_build_occ(const void* plain, int dtype, const int n[3], unsigned long long* occ, cudaStream_t st) {
+  const long blocks = (long)((n[0] + 3) >> 2) * ((n[1] + 3) >> 2) * ((n[2] + 3) >> 2);
+  cudaMemsetAsync(occ, 0, sizeof(unsigned long long) * occ_words(n), st);
+  k_occ<<<(unsigned)((blocks + 127) / 128), 128, 0, st>>>(plain, dtype, n[0], n[1], n[2], occ);
+}
+
 // Nonzero voxels in the box [q0, q1] (inclusive, inside the image).
 static __device__ __forceinline__ long nz_in_box(const int* S, const int* n, const int q0[3], const int q1[3]) {
   const long X = n[0] + 1, XY = X * (n[1] + 1);
@@ -534,7 +560,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       for (int a = 0; a < 3; ++a) in = in && plo[a] >= -0.75f && phi[a] <= (float)np[a] - 0.25f;
       if (flags && in) flags |= 2;
     }
-    if (flags && mapok) flags |= zbits[d];
+    if (flags && mapok) flags |= zbits[d] | 32;
     R4[0] = make_int4(flags, pi, t, d);
     // gx: (1 + G00, G10, G20, black-decision margin delta = 2^-19 M)
     *reinterpret_cast<float4*>(&R.gx[0]) = make_float4(1.0f + G[0][0], G[1][0], G[2][0], M * (1.0f / 524288.0f));

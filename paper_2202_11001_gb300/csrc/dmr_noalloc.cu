@@ -40,8 +40,8 @@ constexpr size_t kOffLoc = al(kOffTrial + 3 * sizeof(int));
 constexpr size_t kOffGterm = al(kOffLoc + 2 * (size_t)kMaxGuide * sizeof(int));
 constexpr size_t kOffSums = al(kOffGterm + 2 * (size_t)kMaxGuide * sizeof(double));
 constexpr size_t kOffSlow = al(kOffSums + 4 * sizeof(double));
-constexpr size_t kOffCount = al(kOffSlow + 2 * (size_t)kMaxTets * sizeof(int));  // samples (u64), work (3 x u32)
-constexpr size_t kScratchBytes = al(kOffCount + 24);
+constexpr size_t kOffCount = al(kOffSlow + 2 * (size_t)kMaxTets * sizeof(int));  // samples, executed (u64), work (3 x u32)
+constexpr size_t kScratchBytes = al(kOffCount + 32);
 
 // The scratch.  Host code must not pass this name to a kernel: on the host it
 // is only a stand-in; the device address comes from cudaGetSymbolAddress.
@@ -62,8 +62,9 @@ __global__ void k_noalloc_init(DevProblem hp, unsigned char* base, int ntet) {
     tr[0] = 0;     // candidate 0 of the scratch problem
     tr[1] = 0;     // first (trial, tet) pair
     tr[2] = ntet;  // all tets
-    *(unsigned long long*)(base + kOffCount) = 0ull;
-    for (int k = 0; k < 3; ++k) ((unsigned*)(base + kOffCount + 8))[k] = 0u;
+    ((unsigned long long*)(base + kOffCount))[0] = 0ull;
+    ((unsigned long long*)(base + kOffCount))[1] = 0ull;
+    for (int k = 0; k < 3; ++k) ((unsigned*)(base + kOffCount + 16))[k] = 0u;
   }
   if (i < ntet) {
     ((int*)(base + kOffTtTrial))[i] = 0;
@@ -129,6 +130,7 @@ extern "C" int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double
   hp.c_gterm = (double*)(base + kOffGterm);
   hp.sums = (double*)(base + kOffSums);
   hp.samples = (unsigned long long*)(base + kOffCount);
+  hp.executed = (unsigned long long*)(base + kOffCount) + 1;
   const DevProblem* d_prob = (const DevProblem*)(base + kOffProb);
   Batch b;
   memset(&b, 0, sizeof(b));
@@ -148,7 +150,7 @@ extern "C" int dmr_eval_one_noalloc(dmr_problem* p, const double* coords, double
   b.o_cov = hp.c_cov;
   b.o_def = hp.c_def;
   b.o_fold = hp.c_fold;
-  b.work = (unsigned*)(base + kOffCount + 8);
+  b.work = (unsigned*)(base + kOffCount + 16);
   b.slow = (int*)(base + kOffSlow);
   k_noalloc_init<<<(hp.ntet + 255) / 256, 256, 0, st>>>(hp, base, hp.ntet);
   launch_setup(d_prob, b, st);

@@ -86,6 +86,7 @@ def load():
         "dmr_plan_kernel_ms": [vp, ip, ip],
         "dmr_set_tile": [vp, i, i],
         "dmr_eval_one_noalloc": [vp, vp, vp],
+        "dmr_sample_counts": [vp, vp, vp, i],
         "dmr_autotune": [vp, i, ip, ip, ip],
         "dmr_batch_create": [i, vp, ctypes.POINTER(ctypes.c_void_p)],
         "dmr_batch_destroy": [vp],
@@ -120,7 +121,7 @@ def exported_symbols():
         "dmr_trial_out", "dmr_samples", "dmr_plan_generation", "dmr_plan_run", "dmr_plan_update", "dmr_plan_destroy",
         "dmr_plan_launches", "dmr_plan_kernel_ms", "dmr_set_tile", "dmr_get_tile", "dmr_autotune", "dmr_batch_create", "dmr_batch_destroy",
         "dmr_batch_plan_generation", "dmr_hypervolume", "dmr_refine", "dmr_link_check", "dmr_mlp_create", "dmr_mlp_destroy", "dmr_mlp_n_params",
-        "dmr_mlp_params", "dmr_mlp_features", "dmr_mlp_forward", "dmr_mlp_train_step", "dmr_eval_one_noalloc", "dmr_last_error",
+        "dmr_mlp_params", "dmr_mlp_features", "dmr_mlp_forward", "dmr_mlp_train_step", "dmr_eval_one_noalloc", "dmr_sample_counts", "dmr_last_error",
     ]
 
 
@@ -434,6 +435,12 @@ class Problem:
         v = ctypes.c_longlong()
         _check(self._lib.dmr_samples(self.h, ctypes.byref(v), int(bool(reset))))
         return v.value
+
+    def sample_counts(self, reset=False):
+        """(counted, executed) voxel-samples since the last reset."""
+        c, e = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.dmr_sample_counts(self.h, ctypes.byref(c), ctypes.byref(e), int(bool(reset))))
+        return c.value, e.value
 
     def plan_generation(self, cand_ids, deltas):
         c = _Arg(cand_ids, np.int32)

@@ -122,7 +122,7 @@ def test_adam_step_matches_reference():
     p1 = net.params().astype(np.float64)
     want, _, _ = ref.adam_step(p0, g.astype(np.float64), np.zeros_like(p0), np.zeros_like(p0), 1, 1e-3)
     d = ref.unpack(np.arange(ref.N_PARAMS))
-    pad = np.concatenate([d["W4"][ref.OUT:].ravel(), d["b4"][ref.OUT:]])
+    pad = np.concatenate([d["W4"][ref.OUT:].ravel(), d["b4"][ref.OUT:]]).astype(np.int64)
     live = np.setdiff1d(np.arange(ref.N_PARAMS), pad)
     assert np.all(p1[pad] == 0.0)
     assert np.allclose(p1[live], want[live], rtol=1e-5, atol=1e-7)
