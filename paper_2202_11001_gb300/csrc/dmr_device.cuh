@@ -288,20 +288,20 @@ static __device__ __forceinline__ void row_span(const ItemRec& r, uint32_t fp, i
   }
 }
 
-// The faces of an item sorted by the sign of A.x: "low" faces (A.x > 0)
-// bound a row from below, "high" faces (A.x < 0) from above, and faces with
-// A.x == 0 (or NaN) are constant along a row.  order holds the face ids in
-// that order, 2 bits each; shape = (number of low faces) | (number of high
-// faces) << 4 (0x13: three low faces and one high face).
-static __device__ __forceinline__ void face_order(const ItemRec& r, int& order, int& shape) {
+// The faces of an item sorted by the sign of A.x (computed by the set-up
+// kernel into the record): "low" faces (A.x > 0) bound a row from below,
+// "high" faces (A.x < 0) from above, and faces with A.x == 0 (or NaN) are
+// constant along a row.  order holds the face ids in that order, 2 bits
+// each; shape = (number of low faces) | (number of high faces) << 4 (0x13:
+// three low faces and one high face).
+static __device__ __forceinline__ void face_order(const float ax[4], int& order, int& shape) {
   int lo_ids = 0, hi_ids = 0, z_ids = 0, nl = 0, nh = 0, nz = 0;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    const float ax = r.fa[f][0];
-    if (ax > 0.f) {
+    if (ax[f] > 0.f) {
       lo_ids |= f << (2 * nl);
       ++nl;
-    } else if (ax < 0.f) {
+    } else if (ax[f] < 0.f) {
       hi_ids |= f << (2 * nh);
       ++nh;
     } else {
@@ -435,7 +435,6 @@ struct WarpSmem {
   ItemRec rec;
   int2 meta[32];     // (exclusive voxel prefix, own plain index of x0) per row
   float4 pr0[32];    // mapped partner-relative coordinate of x0 per row
-  int forder, fshape;  // fast pass: the item's faces sorted by the sign of A.x (face_order)
   // empty-space test of the rows: own and partner block occupancy bitmaps,
   // partner dimensions, mode (0 off, 1 own rows only: the partner region is
   // all 0, 2 own rows and the partner region)
@@ -652,7 +651,6 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
       // on chip).  Its parameters wait in shared memory (read where used, so
       // that they hold no registers across the loops).
       if (lane == 0) {
-        if constexpr (FAST) face_order(r, ws->forder, ws->fshape);
         const unsigned long long* zo = pr.occ[d];
         const unsigned long long* zp = pr.occ[1 - d];
         const bool on = zo != nullptr && zp != nullptr && (r.flags & 32) && !(r.flags & 8);
@@ -701,8 +699,8 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
             int lo, hi;
             const int yi = yrow - Oy, zi = zrow - Oz;
             if constexpr (FAST) {
-              const int forder = *(volatile int*)&ws->forder;
-              switch (*(volatile int*)&ws->fshape) {
+              const int forder = *(volatile int*)&r.forder;
+              switch (*(volatile int*)&r.fshape) {
                 case 0x13: row_span_sorted<3, 1>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
                 case 0x22: row_span_sorted<2, 2>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;
                 case 0x31: row_span_sorted<1, 3>(r, forder, xl, xh, yi, zi, lo, hi, careful); break;

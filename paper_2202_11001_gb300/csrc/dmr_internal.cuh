@@ -90,7 +90,9 @@ struct __align__(16) ItemRec {
   int O[4];         // own origin (floor of min vertex coords)
   int Op[4];        // partner origin
   unsigned cbase;   // corner-cell index offset (mod 2^32, see kernels)
-  int pad0[3];
+  int forder;       // the faces sorted by the sign of their FP32 normal's x (2 bits each)
+  int fshape;       // (faces with A.x > 0) | (faces with A.x < 0) << 4
+  int pad0;
   float vr[4][4];   // own vertices relative to O (x,y,z,-)
   float fa[4][4];   // face f: inward normal A (x,y,z), offset B'
   float fm[4][4];   // face f: margin mu (box points), 1/A.x, margin growth per voxel of |p - O|,

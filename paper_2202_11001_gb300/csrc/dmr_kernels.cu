@@ -508,6 +508,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
                           -((rr[0][2] + rr[1][2]) + rr[2][2])};
     const uint32_t fp = pr.fperm[t];
     const float Lf = (float)L;
+    float axf[4];
     // edge magnitudes are bounded by the box extent: |u|, |w| <= ext
     const float ext = 1.001f * fmaxf(hi[0] - lo[0], fmaxf(hi[1] - lo[1], hi[2] - lo[2]));
     const float UW = ext * ext;
@@ -519,6 +520,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       const double nz = opp == 0 ? N0[2] : opp == 1 ? rr[0][2] : opp == 2 ? rr[1][2] : rr[2][2];
       const double Bd = -fma(nx, pick4d(vd, ia, 0), fma(ny, pick4d(vd, ia, 1), nz * pick4d(vd, ia, 2)));
       const float Ax = (float)nx, Ay = (float)ny, Az = (float)nz, Bp = (float)Bd;
+      axf[f] = Ax;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
       const float mu = (5.0f / 16777216.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
       *reinterpret_cast<float4*>(&R.fa[f][0]) = make_float4(Ax, Ay, Az, Bp);
@@ -572,7 +574,9 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     unsigned Sy = (unsigned)(np[0] + 2), Sz = (unsigned)((np[1] + 2) * (np[0] + 2));
     unsigned base = ((unsigned)(Op[2] + 1) * (unsigned)(np[1] + 2) + (unsigned)(Op[1] + 1)) * Sy + (unsigned)(Op[0] + 1);
     base -= (unsigned)MAGIC_BITS * (Sz + Sy + 1u);
-    R4[5] = make_int4((int)base, 0, 0, 0);
+    int forder, fshape;
+    face_order(axf, forder, fshape);
+    R4[5] = make_int4((int)base, forder, fshape, 0);
   }
   b.o_def[tt] = def;
 }
