@@ -309,7 +309,11 @@ int dmr_mlp_forward(dmr_mlp* mlp, const void* X, int n, float* out);
 /* Gaussian negative log-likelihood of targets Y (device FP32 [n][3]) on
  * batch X; gradient by backpropagation on the tensor cores; if lr > 0 one
  * Adam step.  loss_out (host, may be NULL) = mean loss before the step;
- * grad_out (host FP32 [n_params], may be NULL) = the gradient. */
+ * grad_out (host FP32 [n_params], may be NULL) = the gradient.  With both
+ * NULL the call only enqueues the step on the network's stream and returns
+ * without waiting; a tensor-core wait that gave up (DMR_ETIMEOUT) is then
+ * reported by the next call that returns a loss, a gradient or parameters,
+ * or runs a forward pass. */
 int dmr_mlp_train_step(dmr_mlp* mlp, const void* X, const float* Y, int n, float lr, float* loss_out,
                        float* grad_out);
 

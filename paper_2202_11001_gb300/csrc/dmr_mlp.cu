@@ -315,38 +315,71 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 
 // C (+)= op(A) op(B): A(m,k) = A[m*sam + k*sak], B(n,k) = B[n*sbn + k*sbk]
 // (BF16 or FP32 sources, rounded to BF16), C(m,n) = C[m*scm + n*scn] FP32.
-// One CTA per 128 rows of C, all N (<= 256) columns, K in chunks of 64.
+// CTA (x, y) computes rows 128 x .. + 127, all N (<= 256) columns, over the
+// y-th of gridDim.y contiguous K ranges of kspan (a multiple of 64), in
+// chunks of 64 staged by the CTA's threads into two shared-memory buffers:
+// the tensor core multiplies chunk c while chunk c + 1 is staged.  Operands
+// are read along their contiguous index (coalesced).  With one K range the
+// result goes to C; with several, range y writes its partial product to
+// part[y][M][N] and k_splitk_reduce adds the ranges in order.
 template <typename TA, typename TB>
-__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const TA* __restrict__ A, long sam, long sak,
-                                                 const TB* __restrict__ B, long sbn, long sbk, float* C, long scm,
-                                                 long scn, int accumulate, int* err) {
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int kspan, const TA* __restrict__ A, long sam,
+                                                 long sak, const TB* __restrict__ B, long sbn, long sbk, float* C,
+                                                 long scm, long scn, int accumulate, float* part, int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int Np = (N + 15) & ~15;
   const uint32_t ncols = Np <= 32 ? 32u : (Np <= 64 ? 64u : (Np <= 128 ? 128u : 256u));
-  unsigned char* sA = sm;                 // 128 x 64 BF16 = 16 KB
-  unsigned char* sB = sm + 16384;         // Np x 64 BF16 <= 32 KB
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 16384 + 32768);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + 16384 + 32768 + 8);
+  constexpr uint32_t kStage = 16384 + 32768;  // A 128 x 64 + B <= 256 x 64, BF16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * kStage);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + 2 * kStage + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * 128;
+  const int kb = blockIdx.y * kspan, ke = min(K, kb + kspan);
+  const int nch = ke > kb ? (ke - kb + 63) / 64 : 0;
   if (warp == 0) tmem_alloc(slot, ncols);
-  if (tid == 0) mbar_init(mbar, 1);
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *slot;
-  uint32_t phase = 0;
   bool ok = true;
-  for (int k0 = 0; k0 < K && ok; k0 += 64) {
-    for (int e = tid; e < 128 * 64; e += 128) {
-      int r = e >> 6, kk = e & 63, m = m0 + r, k = k0 + kk;
-      float v = (m < M && k < K) ? (float)A[(size_t)m * sam + (size_t)k * sak] : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(sA + kmaj_off(r, kk, 64)) = __float2bfloat16_rn(v);
+  for (int c = 0; c < nch && ok; ++c) {
+    const int buf = c & 1;
+    unsigned char* sA = sm + buf * kStage;
+    unsigned char* sB = sA + 16384;
+    // the buffer was last read by the MMAs of chunk c - 2
+    if (c >= 2) ok = __syncthreads_and(mbar_wait(mbar + buf, (uint32_t)(((c - 2) >> 1) & 1))) != 0;
+    if (!ok) break;
+    tc_fence_after();
+    const int k0 = kb + 64 * c;
+    if (sak == 1) {
+      for (int e = tid; e < 128 * 64; e += 128) {
+        const int r = e >> 6, kk = e & 63, m = m0 + r, k = k0 + kk;
+        const float v = (m < M && k < ke) ? (float)A[(size_t)m * sam + (size_t)k] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(sA + kmaj_off(r, kk, 64)) = __float2bfloat16_rn(v);
+      }
+    } else {
+      for (int e = tid; e < 128 * 64; e += 128) {
+        const int r = e & 127, kk = e >> 7, m = m0 + r, k = k0 + kk;
+        const float v = (m < M && k < ke) ? (float)A[(size_t)m * sam + (size_t)k * sak] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(sA + kmaj_off(r, kk, 64)) = __float2bfloat16_rn(v);
+      }
     }
-    for (int e = tid; e < Np * 64; e += 128) {
-      int r = e >> 6, kk = e & 63, k = k0 + kk;
-      float v = (r < N && k < K) ? (float)B[(size_t)r * sbn + (size_t)k * sbk] : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(sB + kmaj_off(r, kk, 64)) = __float2bfloat16_rn(v);
+    if (sbk == 1) {
+      for (int e = tid; e < Np * 64; e += 128) {
+        const int r = e >> 6, kk = e & 63, k = k0 + kk;
+        const float v = (r < N && k < ke) ? (float)B[(size_t)r * sbn + (size_t)k] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(sB + kmaj_off(r, kk, 64)) = __float2bfloat16_rn(v);
+      }
+    } else {
+      for (int e = tid; e < Np * 64; e += 128) {
+        const int r = e % Np, kk = e / Np, k = k0 + kk;
+        const float v = (r < N && k < ke) ? (float)B[(size_t)r * sbn + (size_t)k * sbk] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(sB + kmaj_off(r, kk, 64)) = __float2bfloat16_rn(v);
+      }
     }
     fence_async_smem();
     tc_fence_before();
@@ -355,32 +388,44 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const TA* 
       tc_fence_after();
       for (int s = 0; s < 4; ++s)
         mma_bf16(tbase, sdesc(smem_u32(sA) + 256u * s, 128u, 1024u), sdesc(smem_u32(sB) + 256u * s, 128u, 1024u),
-                 idesc_bf16(128, Np), (k0 > 0 || s > 0) ? 1u : 0u);
-      mma_commit(mbar);
+                 idesc_bf16(128, Np), (c > 0 || s > 0) ? 1u : 0u);
+      mma_commit(mbar + buf);  // tracks every MMA issued so far
     }
-    bool w = mbar_wait(mbar, phase);
-    phase ^= 1u;
-    ok = __syncthreads_and(w) != 0;
+  }
+  // the last chunk's commit covers all earlier MMAs
+  if (ok && nch > 0) {
+    const int last = nch - 1;
+    ok = __syncthreads_and(mbar_wait(mbar + (last & 1), (uint32_t)((last >> 1) & 1))) != 0;
     tc_fence_after();
   }
-  if (ok && K > 0) {
+  if (ok) {
     const int m = m0 + 32 * warp + lane;
     const uint32_t lb = tbase + ((uint32_t)(32 * warp) << 16);
     for (int c0 = 0; c0 < Np; c0 += 16) {
       float v[16];
-      tmem_ld16(lb + (uint32_t)c0, v);
+      if (nch > 0) {
+        tmem_ld16(lb + (uint32_t)c0, v);
+      } else {
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      }
       if (m < M)
         for (int j = 0; j < 16; ++j) {
-          int n = c0 + j;
+          const int n = c0 + j;
           if (n < N) {
-            float* dst = C + (size_t)m * scm + (size_t)n * scn;
-            *dst = accumulate ? *dst + v[j] : v[j];
+            if (gridDim.y > 1) {
+              part[((size_t)blockIdx.y * M + m) * N + n] = v[j];
+            } else {
+              float* dst = C + (size_t)m * scm + (size_t)n * scn;
+              *dst = accumulate ? *dst + v[j] : v[j];
+            }
           }
         }
     }
-  } else if (!ok) {
+  } else {
     if (tid == 0) atomicExch(err, kErrTimeout);
-    (void)mbar_wait(mbar, phase ^ 1u);
+    // give outstanding commits one more bounded chance before the tensor
+    // memory is released
+    if (nch > 0) (void)mbar_wait(mbar + ((nch - 1) & 1), (uint32_t)(((nch - 1) >> 1) & 1));
   }
   tc_fence_before();
   __syncthreads();
@@ -388,6 +433,19 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const TA* 
     tc_fence_after();
     tmem_dealloc(tbase, ncols);
   }
+}
+
+// C (+)= sum over the K ranges of their partial products part[S][M][N], in
+// range order (deterministic).
+__global__ void k_splitk_reduce(int M, int N, int S, const float* __restrict__ part, float* C, long scm, long scn,
+                                int accumulate) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)M * N) return;
+  const int m = (int)(i / N), n = (int)(i % N);
+  float acc = 0.f;
+  for (int y = 0; y < S; ++y) acc += part[((size_t)y * M + m) * N + n];
+  float* dst = C + (size_t)m * scm + (size_t)n * scn;
+  *dst = accumulate ? *dst + acc : acc;
 }
 
 // Features of (candidate, point) rows: 5x5x5 trilinear samples of the source
@@ -462,13 +520,24 @@ __global__ void k_gelu_back(const float* __restrict__ dH, const float* __restric
   if (i < count) dZ[i] = dH[i] * gelu_grad(Z[i]);
 }
 
-// Column sums of dZ [n][cols] into g[cols] (one thread per column, ordered).
-__global__ void k_colsum(const float* __restrict__ dZ, int n, int cols, float* g) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+// Column sums of dZ [n][cols] into g[cols]: a CTA of 32 x 32 threads per 32
+// columns; thread (x, y) adds rows y, y + 32, ... of column x in FP64 (a warp
+// reads 32 consecutive columns of a row), then the 32 partial sums of a
+// column are added in order of y (deterministic).
+__global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ dZ, int n, int cols, float* g) {
+  __shared__ double part[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx;
   double s = 0.0;
-  for (int i = 0; i < n; ++i) s += dZ[(size_t)i * cols + c];
-  g[c] = (float)s;
+  if (c < cols)
+    for (int i = ty; i < n; i += 32) s += dZ[(size_t)i * cols + c];
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && c < cols) {
+    double t = 0.0;
+    for (int y = 0; y < 32; ++y) t += part[y][tx];
+    g[c] = (float)t;
+  }
 }
 
 __global__ void k_adam(float* P, const float* G, float* m, float* v, int count, float lr, float b1, float b2,
@@ -492,16 +561,37 @@ __global__ void k_to_bf16(const float* P, __nv_bfloat16* Wb, int count) {
   if (i < count) Wb[i] = __float2bfloat16_rn(P[i]);
 }
 
+// Largest number of K ranges a product is split into, and the partial-product
+// workspace it needs (ranges x 128 x 256 FP32 for the weight gradients).
+constexpr int kMaxSplit = 64;
+constexpr size_t kSplitWs = (size_t)kMaxSplit * 128 * 256;
+
+// C (+)= op(A) op(B) on the tensor cores.  A product with few row tiles and a
+// long K (the weight gradients: M = 128 outputs, K = batch rows) is split
+// into K ranges so that about two CTAs per SM work on it; the ranges' partial
+// products are added by k_splitk_reduce.
 template <typename TA, typename TB>
 void gemm(int M, int N, int K, const TA* A, long sam, long sak, const TB* B, long sbn, long sbk, float* C, long scm,
-          long scn, int acc, int* err, cudaStream_t st) {
-  const size_t smem = 16384 + 32768 + 16;
+          long scn, int acc, int* err, float* ws, int n_sm, cudaStream_t st) {
+  const size_t smem = 2 * (16384 + 32768) + 32;
   static bool once = false;
   if (!once) {
     cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     once = true;
   }
-  k_gemm_tc<TA, TB><<<(M + 127) / 128, 128, smem, st>>>(M, N, K, A, sam, sak, B, sbn, sbk, C, scm, scn, acc, err);
+  const int mt = (M + 127) / 128, chunks = (K + 63) / 64;
+  int S = std::min(std::max(1, (2 * n_sm + mt - 1) / mt), std::max(1, chunks / 2));
+  if ((size_t)S * M * N > kSplitWs) S = std::max(1, (int)(kSplitWs / ((size_t)M * N)));
+  S = std::min(S, kMaxSplit);
+  const int kspan = 64 * ((chunks + S - 1) / S);
+  S = (K + kspan - 1) / kspan;
+  if (S < 1) S = 1;
+  k_gemm_tc<TA, TB><<<dim3(mt, S), 128, smem, st>>>(M, N, K, kspan, A, sam, sak, B, sbn, sbk, C, scm, scn, acc,
+                                                     S > 1 ? ws : nullptr, err);
+  if (S > 1) {
+    const long cnt = (long)M * N;
+    k_splitk_reduce<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(M, N, S, ws, C, scm, scn, acc);
+  }
 }
 
 }  // namespace
@@ -524,6 +614,7 @@ struct dmr_mlp {
   int cap = 0;
   float *out = nullptr, *Zs = nullptr, *dZ4 = nullptr, *dH = nullptr, *dZ = nullptr;
   __nv_bfloat16* Hs = nullptr;
+  float* split = nullptr;  // partial products of split-K weight gradients
 };
 
 namespace {
@@ -599,7 +690,7 @@ int dmr_mlp_create(unsigned long long seed, void* stream, dmr_mlp** out) {
   int rc;
   if ((rc = mlp_alloc(&M->P, kNParams)) || (rc = mlp_alloc(&M->G, kNParams)) || (rc = mlp_alloc(&M->m, kNParams)) ||
       (rc = mlp_alloc(&M->v, kNParams)) || (rc = mlp_alloc(&M->Wb, kNParams)) || (rc = mlp_alloc(&M->err, 1)) ||
-      (rc = mlp_alloc(&M->loss, 1))) {
+      (rc = mlp_alloc(&M->loss, 1)) || (rc = mlp_alloc(&M->split, kSplitWs))) {
     dmr_mlp_destroy(M);
     return rc;
   }
@@ -637,6 +728,7 @@ int dmr_mlp_destroy(dmr_mlp* M) {
   cudaFree(M->P); cudaFree(M->G); cudaFree(M->m); cudaFree(M->v); cudaFree(M->Wb); cudaFree(M->err);
   cudaFree(M->loss); cudaFree(M->out); cudaFree(M->Zs); cudaFree(M->dZ4); cudaFree(M->dH); cudaFree(M->dZ);
   cudaFree(M->Hs);
+  cudaFree(M->split);
   delete M;
   return DMR_OK;
 }
@@ -654,7 +746,8 @@ int dmr_mlp_params(dmr_mlp* M, float* get, const float* set) {
     M->t = 0;
   }
   if (get) {
-    cudaStreamSynchronize(M->st);
+    const int rc = check_err(M);  // synchronises; reports an earlier step's timeout
+    if (rc) return rc;
     if (cudaMemcpy(get, M->P, sizeof(float) * kNParams, cudaMemcpyDefault) != cudaSuccess)
       return set_error(DMR_ECUDA, "mlp get params");
   }
@@ -699,23 +792,25 @@ int dmr_mlp_train_step(dmr_mlp* M, const void* Xv, const float* Y, int n, float 
   const __nv_bfloat16* H[3] = {M->Hs, M->Hs + (size_t)n * kHid, M->Hs + 2 * (size_t)n * kHid};
   const float* Z[3] = {M->Zs, M->Zs + (size_t)n * kHid, M->Zs + 2 * (size_t)n * kHid};
   // layer 4: dW4^T = H3^T dZ4 (M=128 in, N=16 out, K=n); b4; dH3 = dZ4 W4
-  gemm(kHid, kOutP, n, H[2], 1, kHid, M->dZ4, 1, kOutP, G + kOffW4, 1, kHid, 0, M->err, st);
-  k_colsum<<<1, 32, 0, st>>>(M->dZ4, n, kOutP, G + kOffB4);
-  gemm(n, kHid, kOutP, M->dZ4, kOutP, 1, W + kOffW4, 1, kHid, M->dH, kHid, 1, 0, M->err, st);
+  float* ws = M->split;
+  const int nsm = M->n_sm;
+  gemm(kHid, kOutP, n, H[2], 1, kHid, M->dZ4, 1, kOutP, G + kOffW4, 1, kHid, 0, M->err, ws, nsm, st);
+  k_colsum<<<(kOutP + 31) / 32, 1024, 0, st>>>(M->dZ4, n, kOutP, G + kOffB4);
+  gemm(n, kHid, kOutP, M->dZ4, kOutP, 1, W + kOffW4, 1, kHid, M->dH, kHid, 1, 0, M->err, ws, nsm, st);
   // layers 3..1
   const int offW[3] = {kOffW1, kOffW2, kOffW3}, offB[3] = {kOffB1, kOffB2, kOffB3};
   for (int l = 2; l >= 0; --l) {
     long cnt = (long)n * kHid;
     k_gelu_back<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(M->dH, Z[l], M->dZ, cnt);
-    k_colsum<<<1, 128, 0, st>>>(M->dZ, n, kHid, G + offB[l]);
+    k_colsum<<<(kHid + 31) / 32, 1024, 0, st>>>(M->dZ, n, kHid, G + offB[l]);
     const int in = l == 0 ? kIn : kHid;
     // dW_l = dZ^T * input (M=128 out, N=in, K=n)
     if (l == 0)
-      gemm(kHid, kIn, n, M->dZ, 1, kHid, X, 1, kIn, G + offW[l], kIn, 1, 0, M->err, st);
+      gemm(kHid, kIn, n, M->dZ, 1, kHid, X, 1, kIn, G + offW[l], kIn, 1, 0, M->err, ws, nsm, st);
     else
-      gemm(kHid, kHid, n, M->dZ, 1, kHid, H[l - 1], 1, kHid, G + offW[l], kHid, 1, 0, M->err, st);
+      gemm(kHid, kHid, n, M->dZ, 1, kHid, H[l - 1], 1, kHid, G + offW[l], kHid, 1, 0, M->err, ws, nsm, st);
     // dH_{l-1} = dZ W_l (M=n, N=in, K=128)
-    if (l > 0) gemm(n, in, kHid, M->dZ, kHid, 1, W + offW[l], 1, in, M->dH, in, 1, 0, M->err, st);
+    if (l > 0) gemm(n, in, kHid, M->dZ, kHid, 1, W + offW[l], 1, in, M->dH, in, 1, 0, M->err, ws, nsm, st);
   }
   if (cudaGetLastError() != cudaSuccess) return set_error(DMR_ECUDA, "mlp backward launch");
   if (lr > 0) {
@@ -723,6 +818,11 @@ int dmr_mlp_train_step(dmr_mlp* M, const void* Xv, const float* Y, int n, float 
     const float b1 = 0.9f, b2 = 0.999f;
     float c1 = 1.f - std::pow(b1, (float)M->t), c2 = 1.f - std::pow(b2, (float)M->t);
     k_adam<<<(kNParams + 255) / 256, 256, 0, st>>>(M->P, G, M->m, M->v, kNParams, lr, b1, b2, 1e-8f, c1, c2, M->Wb);
+  }
+  if (!loss_out && !grad_out) {
+    // nothing to return to the host: no synchronisation; a tensor-core wait
+    // that gave up is reported by the next call that synchronises
+    return cudaGetLastError() == cudaSuccess ? DMR_OK : set_error(DMR_ECUDA, "mlp train launch");
   }
   rc = check_err(M);
   if (rc) return rc;

@@ -567,12 +567,18 @@ class MLP:
         _check(self._lib.dmr_mlp_forward(self.h, Xc.data_ptr(), X.shape[0], out.data_ptr()))
         return out
 
-    def train_step(self, X, Y, lr, want_grad=False):
+    def train_step(self, X, Y, lr, want_grad=False, want_loss=True):
+        """One step; returns the loss (and the gradient with want_grad).  With
+        want_loss=False and no gradient the step is only enqueued (returns
+        None) and the inputs must stay alive until the stream reaches it."""
         Xc, Yc = X.contiguous(), Y.contiguous().float()
         loss = ctypes.c_float()
         g = np.zeros(self.n_params, np.float32) if want_grad else None
-        _check(self._lib.dmr_mlp_train_step(self.h, Xc.data_ptr(), Yc.data_ptr(), X.shape[0], float(lr),
-                                            ctypes.addressof(loss), g.ctypes.data if g is not None else None))
+        lp = ctypes.addressof(loss) if (want_loss or want_grad) else None
+        _check(self._lib.dmr_mlp_train_step(self.h, Xc.data_ptr(), Yc.data_ptr(), X.shape[0], float(lr), lp,
+                                            g.ctypes.data if g is not None else None))
+        if lp is None:
+            return None
         return (loss.value, g) if want_grad else loss.value
 
     def close(self):
