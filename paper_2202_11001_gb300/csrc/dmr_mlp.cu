@@ -520,24 +520,25 @@ __global__ void k_gelu_back(const float* __restrict__ dH, const float* __restric
   if (i < count) dZ[i] = dH[i] * gelu_grad(Z[i]);
 }
 
-// Column sums of dZ [n][cols] into g[cols]: a CTA of 32 x 32 threads per 32
-// columns; thread (x, y) adds rows y, y + 32, ... of column x in FP64 (a warp
-// reads 32 consecutive columns of a row), then the 32 partial sums of a
-// column are added in order of y (deterministic).
-__global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ dZ, int n, int cols, float* g) {
-  __shared__ double part[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + tx;
+// Column sums of dZ [n][cols] into g[cols], in two passes: CTA b adds rows
+// 128 b .. 128 b + 127 of every column (thread c takes column c, so a warp
+// reads consecutive columns of a row) into part[b][cols]; k_colsum_fin adds
+// the partial sums of a column in order of b (deterministic).
+constexpr int kColRows = 128;
+__global__ void k_colsum_part(const float* __restrict__ dZ, int n, int cols, float* part) {
+  const int c = threadIdx.x, r0 = blockIdx.x * kColRows;
+  if (c >= cols) return;
+  float s = 0.f;
+  const int r1 = min(n, r0 + kColRows);
+  for (int i = r0; i < r1; ++i) s += dZ[(size_t)i * cols + c];
+  part[(size_t)blockIdx.x * cols + c] = s;
+}
+__global__ void k_colsum_fin(const float* __restrict__ part, int groups, int cols, float* g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
   double s = 0.0;
-  if (c < cols)
-    for (int i = ty; i < n; i += 32) s += dZ[(size_t)i * cols + c];
-  part[ty][tx] = s;
-  __syncthreads();
-  if (ty == 0 && c < cols) {
-    double t = 0.0;
-    for (int y = 0; y < 32; ++y) t += part[y][tx];
-    g[c] = (float)t;
-  }
+  for (int b = 0; b < groups; ++b) s += part[(size_t)b * cols + c];
+  g[c] = (float)s;
 }
 
 __global__ void k_adam(float* P, const float* G, float* m, float* v, int count, float lr, float b1, float b2,
@@ -562,7 +563,8 @@ __global__ void k_to_bf16(const float* P, __nv_bfloat16* Wb, int count) {
 }
 
 // Largest number of K ranges a product is split into, and the partial-product
-// workspace it needs (ranges x 128 x 256 FP32 for the weight gradients).
+// workspace it needs (ranges x 128 x 256 FP32 for the weight gradients; the
+// column sums of the bias gradients use it too).
 constexpr int kMaxSplit = 64;
 constexpr size_t kSplitWs = (size_t)kMaxSplit * 128 * 256;
 
@@ -580,7 +582,7 @@ void gemm(int M, int N, int K, const TA* A, long sam, long sak, const TB* B, lon
     once = true;
   }
   const int mt = (M + 127) / 128, chunks = (K + 63) / 64;
-  int S = std::min(std::max(1, (2 * n_sm + mt - 1) / mt), std::max(1, chunks / 2));
+  int S = std::min(std::max(1, (2 * n_sm + mt - 1) / mt), chunks);
   if ((size_t)S * M * N > kSplitWs) S = std::max(1, (int)(kSplitWs / ((size_t)M * N)));
   S = std::min(S, kMaxSplit);
   const int kspan = 64 * ((chunks + S - 1) / S);
@@ -592,6 +594,12 @@ void gemm(int M, int N, int K, const TA* A, long sam, long sak, const TB* B, lon
     const long cnt = (long)M * N;
     k_splitk_reduce<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(M, N, S, ws, C, scm, scn, acc);
   }
+}
+
+void colsum(const float* dZ, int n, int cols, float* g, float* ws, cudaStream_t st) {
+  const int groups = (n + kColRows - 1) / kColRows;
+  k_colsum_part<<<groups, cols, 0, st>>>(dZ, n, cols, ws);
+  k_colsum_fin<<<(cols + 127) / 128, 128, 0, st>>>(ws, groups, cols, g);
 }
 
 }  // namespace
@@ -780,6 +788,8 @@ int dmr_mlp_forward(dmr_mlp* M, const void* X, int n, float* out) {
 int dmr_mlp_train_step(dmr_mlp* M, const void* Xv, const float* Y, int n, float lr, float* loss_out,
                        float* grad_out) {
   if (!M || !Xv || !Y || n < 1) return set_error(DMR_EINVAL, "bad mlp train arguments");
+  if ((size_t)((n + kColRows - 1) / kColRows) * kHid > kSplitWs)
+    return set_error(DMR_EINVAL, "mlp train: batch above " + std::to_string(kSplitWs / kHid * kColRows) + " rows");
   int rc = ensure_ws(M, n);
   if (rc) return rc;
   const __nv_bfloat16* X = (const __nv_bfloat16*)Xv;
@@ -795,14 +805,14 @@ int dmr_mlp_train_step(dmr_mlp* M, const void* Xv, const float* Y, int n, float 
   float* ws = M->split;
   const int nsm = M->n_sm;
   gemm(kHid, kOutP, n, H[2], 1, kHid, M->dZ4, 1, kOutP, G + kOffW4, 1, kHid, 0, M->err, ws, nsm, st);
-  k_colsum<<<(kOutP + 31) / 32, 1024, 0, st>>>(M->dZ4, n, kOutP, G + kOffB4);
+  colsum(M->dZ4, n, kOutP, G + kOffB4, ws, st);
   gemm(n, kHid, kOutP, M->dZ4, kOutP, 1, W + kOffW4, 1, kHid, M->dH, kHid, 1, 0, M->err, ws, nsm, st);
   // layers 3..1
   const int offW[3] = {kOffW1, kOffW2, kOffW3}, offB[3] = {kOffB1, kOffB2, kOffB3};
   for (int l = 2; l >= 0; --l) {
     long cnt = (long)n * kHid;
     k_gelu_back<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(M->dH, Z[l], M->dZ, cnt);
-    k_colsum<<<(kHid + 31) / 32, 1024, 0, st>>>(M->dZ, n, kHid, G + offB[l]);
+    colsum(M->dZ, n, kHid, G + offB[l], ws, st);
     const int in = l == 0 ? kIn : kHid;
     // dW_l = dZ^T * input (M=128 out, N=in, K=n)
     if (l == 0)
