@@ -443,6 +443,11 @@ struct WarpSmem {
   int zn[3];
   int zon;
   unsigned execd;  // samples of the current item mapped and sampled so far
+  // loop state parked here while the voxel loop runs (it holds no registers
+  // there): per slice lane the first row index and first y of its slice, the
+  // slice group, the batch, the rows of the group, the own image's nx and ny
+  int yex[32], ylos[32];
+  int zb, R, nxo, nyo;
 };
 
 template <int ST>
@@ -633,15 +638,11 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
       const void* cells = pr.cells[1 - d];
       const uint8_t* cflag = pr.cflag[1 - d];
       const unsigned long long* cmask = pr.cmask[1 - d];
-      const int nxo = pr.n[d][0], nyo = pr.n[d][1];
       const unsigned Sy = (unsigned)(pr.n[1 - d][0] + 2), Sz = (unsigned)(pr.n[1 - d][1] + 2) * Sy;
       const bool black = pr.black_rule != 0;
       const bool pzero = (r.flags & 4) != 0;
       // cell flags are read only where a sample may be black
       const bool cfload = black && !(r.flags & 8);
-      const int Ox = r.O[0], Oy = r.O[1], Oz = r.O[2];
-      const int xl = r.b0[0] - Ox, xh = r.b1[0] - Ox;
-      const int by0 = r.b0[1], by1 = r.b1[1];
       // empty-space test per row: a row whose own voxels are all 0 and whose
       // samples can reach only partner voxels that are 0 adds exactly 0
       // (every sample is 0 and black: black against black, or 0 - 0), so it
@@ -659,26 +660,35 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
         ws->zon = on ? (pzero ? 1 : 2) : 0;
         for (int a = 0; a < 3; ++a) ws->zn[a] = pr.n[1 - d][a];
         ws->execd = 0u;
+        ws->nxo = pr.n[d][0];
+        ws->nyo = pr.n[d][1];
       }
       __syncwarp();
-      for (int zb = r.b0[2]; zb <= r.b1[2]; zb += 32) {
+      // the record's integer fields, read where used
+#define RV(f) (*(volatile int*)&(f))
+      for (int zb = r.b0[2]; zb <= RV(r.b1[2]); zb = RV(ws->zb) + 32) {
         const int z = zb + lane;
+        const int Oy = RV(r.O[1]);
         int ycnt = 0, ylo = 0;
-        if (z <= r.b1[2]) {
+        if (z <= RV(r.b1[2])) {
           float ylf, yhf;
-          slice_yrange(r, (float)(z - Oz), ylf, yhf);
+          slice_yrange(r, (float)(z - RV(r.O[2])), ylf, yhf);
           float slack = 1.0f / 256.0f + 1e-5f * fabsf(yhf);
-          int y0 = max(by0, (int)ceilf(ylf - slack) + Oy);
-          int y1 = min(by1, (int)floorf(yhf + slack) + Oy);
+          int y0 = max(RV(r.b0[1]), (int)ceilf(ylf - slack) + Oy);
+          int y1 = min(RV(r.b1[1]), (int)floorf(yhf + slack) + Oy);
           if (ylf <= yhf && y1 >= y0) {
             ylo = y0;
             ycnt = y1 - y0 + 1;
           }
         }
         const int yincl = warp_incl_scan(ycnt, lane);
-        const int yexcl = yincl - ycnt;
-        const int R = __shfl_sync(FULL_MASK, yincl, 31);
-        for (int rb = cta_mode ? 32 * wid : 0; rb < R; rb += rstep) {
+        ws->yex[lane] = yincl - ycnt;
+        ws->ylos[lane] = ylo;
+        ws->zb = zb;  // every lane stores the same value
+        if (lane == 31) ws->R = yincl;
+        __syncwarp();
+        for (int rb = cta_mode ? 32 * wid : 0; rb < RV(ws->R); rb += rstep) {
+          const int R = RV(ws->R);
           const int rr = rb + lane;
           const bool has_row = rr < R;
           const int rq = has_row ? rr : R - 1;
@@ -686,16 +696,21 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
 #pragma unroll
           for (int step = 16; step > 0; step >>= 1) {
             const int cs = s + step;
-            const int e = __shfl_sync(FULL_MASK, yexcl, cs & 31);
+            const int e = RV(ws->yex[cs & 31]);
             if (cs < 32 && e <= rq) s = cs;
           }
-          const int e_s = __shfl_sync(FULL_MASK, yexcl, s);
-          const int yl_s = __shfl_sync(FULL_MASK, ylo, s);
-          const int zrow = zb + s;
+          const int e_s = RV(ws->yex[s]);
+          const int yl_s = RV(ws->ylos[s]);
+          const int zrow = RV(ws->zb) + s;
           const int yrow = yl_s + (rq - e_s);
+          const int Ox = RV(r.O[0]);
+          const int xl = RV(r.b0[0]) - Ox, xh = RV(r.b1[0]) - Ox;
+          const int nxo = RV(ws->nxo), nyo = RV(ws->nyo);
           int xcnt = 0, x0 = 0;
           bool careful = false;
           if (has_row) {
+            const int Oy = RV(r.O[1]), Oz = RV(r.O[2]);
+            const uint32_t fp = pr.fperm[RV(r.tet)];
             int lo, hi;
             const int yi = yrow - Oy, zi = zrow - Oz;
             if constexpr (FAST) {
@@ -736,7 +751,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
               // p + (xcnt - 1) gx (the loop's own expressions, monotone in the
               // step, clamps included); every exact support lies within 1 voxel
               // below / 2 above the FP32 cell, clamped to the image
-              const float vx = (float)(x0 - Ox), vy = (float)(yrow - Oy), vz = (float)(zrow - Oz);
+              const float vx = (float)(x0 - Ox), vy = (float)(yrow - RV(r.O[1])), vz = (float)(zrow - RV(r.O[2]));
               const float4 g0 = lds4(&r.G[0][0]), g1 = lds4(&r.G[1][0]), g2 = lds4(&r.G[2][0]);
               const float4 gx = lds4(&r.gx[0]), lo = lds4(&r.clo[0]), hi = lds4(&r.chi[0]);
               const float dl = (float)(xcnt - 1);
@@ -773,7 +788,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           const int T = __shfl_sync(FULL_MASK, xincl, 31);
           if (T == 0) continue;
           if (xs > 0) {
-            const float vx = (float)(x0 - Ox), vy = (float)(yrow - Oy), vz = (float)(zrow - Oz);
+            const float vx = (float)(x0 - Ox), vy = (float)(yrow - RV(r.O[1])), vz = (float)(zrow - RV(r.O[2]));
             const float4 g0 = lds4(&r.G[0][0]), g1 = lds4(&r.G[1][0]), g2 = lds4(&r.G[2][0]);
             const float px = vx + fmaf(g0.x, vx, fmaf(g0.y, vy, fmaf(g0.z, vz, g0.w)));
             const float py = vy + fmaf(g1.x, vx, fmaf(g1.y, vy, fmaf(g1.z, vz, g1.w)));
