@@ -800,6 +800,8 @@ def main():
     ap.add_argument("--tile", default="", help="fixed raster tile WARPSxVOXELS (e.g. 4x32) instead of autotuning")
     ap.add_argument("--problems", type=int, default=0,
                     help="batch64: only the first N problems (small profiling captures; not a bench line)")
+    ap.add_argument("--population", type=int, default=0,
+                    help="single-problem workloads: only the first N candidates (small profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3")
@@ -831,6 +833,8 @@ def main():
     from paper_2202_11001_gb300 import dmr, synth
 
     pr = workload(args.workload, rank)
+    if args.population:
+        pr["coords"] = np.ascontiguousarray(pr["coords"][: args.population])
     C = pr["coords"].shape[0]
     src, tgt = pr["img"]
     stream = torch.cuda.current_stream().cuda_stream

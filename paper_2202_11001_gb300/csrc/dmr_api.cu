@@ -1352,12 +1352,19 @@ int build_plan(const std::vector<dmr_problem*>& probs, const DevProblem* d_probs
       if (w >= (int)p->wave_ptr.size() - 1) continue;
       const int Gq = p->gmax;
       const int nc = (int)cands[q].size();
+      // trials group-major (every candidate of a group, then the next group):
+      // consecutive raster items then sample the same image region, which
+      // stays in L2 across the candidates; each candidate's trial list (for
+      // the sums) keeps its groups in wave order
+      const int ng_w = p->wave_ptr[w + 1] - p->wave_ptr[w];
       for (int ci = 0; ci < nc; ++ci) {
-        cptr.push_back(k);
+        cptr.push_back((int)ctr.size() - w_tr0.back());  // position in this wave's list
         ++nlist;
-        for (int gi = p->wave_ptr[w]; gi < p->wave_ptr[w + 1]; ++gi, ++k) {
+        for (int j = 0; j < ng_w; ++j) ctr.push_back(k + j * nc + ci);
+      }
+      for (int gi = p->wave_ptr[w]; gi < p->wave_ptr[w + 1]; ++gi) {
+        for (int ci = 0; ci < nc; ++ci, ++k) {
           const int g = p->wave_groups[gi];
-          ctr.push_back(k);
           tr_cand.push_back(cands[q][ci]);
           tr_group.push_back(goff[q] + g);
           tr_prob.push_back(q);
