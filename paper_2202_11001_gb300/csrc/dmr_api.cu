@@ -182,6 +182,7 @@ struct dmr_problem {
   unsigned long long* cmask[2] = {nullptr, nullptr};
   int* nzsat[2] = {nullptr, nullptr};
   unsigned long long* occ[2] = {nullptr, nullptr};
+  unsigned long long* occd[2] = {nullptr, nullptr};
   int4* d_tet = nullptr;
   uint32_t* d_fperm = nullptr;
   uint8_t* d_fix = nullptr;
@@ -353,6 +354,7 @@ void release_problem(dmr_problem* p) {
     dfree(p->cmask[k]);
     dfree(p->nzsat[k]);
     dfree(p->occ[k]);
+    dfree(p->occd[k]);
   }
   dfree(p->d_tet); dfree(p->d_fperm); dfree(p->d_fix); dfree(p->d_restvol); dfree(p->d_guide);
   dfree(p->d_star_ptr); dfree(p->d_star);
@@ -483,9 +485,12 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       // nonzero counts fit an int below 2^31 voxels; larger images go without
       const long ns = (long)(p->n[k][0] + 1) * (p->n[k][1] + 1) * (p->n[k][2] + 1);
       if (nv < (1L << 31)) {
-        if ((rc = dalloc(&p->nzsat[k], ns)) || (rc = dalloc(&p->occ[k], occ_words(p->n[k])))) goto fail_;
+        if ((rc = dalloc(&p->nzsat[k], ns)) || (rc = dalloc(&p->occ[k], occ_words(p->n[k]))) ||
+            (rc = dalloc(&p->occd[k], occ_words(p->n[k]))))
+          goto fail_;
         launch_build_nzsat(p->plain[k], p->storage, p->n[k], p->nzsat[k], p->st);
         launch_build_occ(p->plain[k], p->storage, p->n[k], p->occ[k], p->st);
+        launch_dilate_occ(p->occ[k], p->n[k], p->occd[k], p->st);
       }
     }
     if (tmp) {
@@ -571,6 +576,7 @@ int dmr_problem_create(const dmr_problem_desc* d, dmr_problem** out) {
       h.cmask[k] = p->cmask[k];
       h.nzsat[k] = p->nzsat[k];
       h.occ[k] = p->occ[k];
+      h.occd[k] = p->occd[k];
       for (int a = 0; a < 3; ++a) {
         h.n[k][a] = p->n[k][a];
         h.spd[k][a] = p->sp[k][a];

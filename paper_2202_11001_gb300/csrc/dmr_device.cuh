@@ -430,6 +430,20 @@ static __device__ __forceinline__ bool occ_box_zero(const unsigned long long* __
   return true;
 }
 
+// True when the 4x4x4 blocks bx0..bx1 of block row (by, bz) of a bitmap
+// (DevProblem::occ layout, BY = ceil(ny / 4), W words per block row) are
+// all clear; one word, or two where the range crosses a word.
+static __device__ __forceinline__ bool occ_blocks_clear(const unsigned long long* __restrict__ occ, int BY, int W,
+                                                        int bx0, int bx1, int by, int bz) {
+  const unsigned long long* row = occ + ((long)bz * BY + by) * W;
+  const int w0 = bx0 >> 6, w1 = bx1 >> 6;
+  if (w0 == w1) return !(__ldg(row + w0) & (~0ull >> (63 - (bx1 & 63))) & (~0ull << (bx0 & 63)));
+  if (__ldg(row + w0) & (~0ull << (bx0 & 63))) return false;
+  for (int w = w0 + 1; w < w1; ++w)
+    if (__ldg(row + w)) return false;
+  return !(__ldg(row + w1) & (~0ull >> (63 - (bx1 & 63))));
+}
+
 // ------------------------------------------------------------ raster + sample
 struct WarpSmem {
   ItemRec rec;
@@ -653,7 +667,7 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
       // that they hold no registers across the loops).
       if (lane == 0) {
         const unsigned long long* zo = pr.occ[d];
-        const unsigned long long* zp = pr.occ[1 - d];
+        const unsigned long long* zp = pr.occd[1 - d];
         const bool on = zo != nullptr && zp != nullptr && (r.flags & 32) && !(r.flags & 8);
         ws->zown = zo;
         ws->zpar = zp;
@@ -744,13 +758,13 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
           }
           int xs = xcnt;  // voxels of this row that are sampled
           if (xcnt > 0 && *(volatile int*)&ws->zon) {
-            bool skip = occ_box_zero(*(const unsigned long long* volatile*)&ws->zown, nxo, nyo, x0, yrow, zrow,
-                                     x0 + xcnt - 1, yrow, zrow);
+            bool skip = occ_blocks_clear(*(const unsigned long long* volatile*)&ws->zown, (nyo + 3) >> 2,
+                                         (((nxo + 3) >> 2) + 63) >> 6, x0 >> 2, (x0 + xcnt - 1) >> 2, yrow >> 2,
+                                         zrow >> 2);
             if (skip && *(volatile int*)&ws->zon == 2) {
               // the samples' FP32 positions run from the row start p to
               // p + (xcnt - 1) gx (the loop's own expressions, monotone in the
-              // step, clamps included); every exact support lies within 1 voxel
-              // below / 2 above the FP32 cell, clamped to the image
+              // step, clamps included)
               const float vx = (float)(x0 - Ox), vy = (float)(yrow - RV(r.O[1])), vz = (float)(zrow - RV(r.O[2]));
               const float4 g0 = lds4(&r.G[0][0]), g1 = lds4(&r.G[1][0]), g2 = lds4(&r.G[2][0]);
               const float4 gx = lds4(&r.gx[0]), lo = lds4(&r.clo[0]), hi = lds4(&r.chi[0]);
@@ -767,17 +781,25 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
                 qy = fminf(fmaxf(qy, lo.y), hi.y);
                 qz = fminf(fmaxf(qz, lo.z), hi.z);
               }
+              // blocks holding the samples' FP32 positions, against the
+              // partner bitmap dilated by one block: a sample's exact support
+              // and FP32 cell lie within 1 voxel below / 2 above its position,
+              // inside the block around the position's block
               int zn[3];
               for (int a = 0; a < 3; ++a) zn[a] = *(volatile int*)&ws->zn[a];
-              const int lx = max((int)floorf(fminf(ax, qx)) - 1 + *(volatile int*)&r.Op[0], 0);
-              const int ly = max((int)floorf(fminf(ay, qy)) - 1 + *(volatile int*)&r.Op[1], 0);
-              const int lz = max((int)floorf(fminf(az, qz)) - 1 + *(volatile int*)&r.Op[2], 0);
-              const int hx = min((int)floorf(fmaxf(ax, qx)) + 2 + *(volatile int*)&r.Op[0], zn[0] - 1);
-              const int hy = min((int)floorf(fmaxf(ay, qy)) + 2 + *(volatile int*)&r.Op[1], zn[1] - 1);
-              const int hz = min((int)floorf(fmaxf(az, qz)) + 2 + *(volatile int*)&r.Op[2], zn[2] - 1);
-              skip = lx > hx || ly > hy || lz > hz ||
-                     occ_box_zero(*(const unsigned long long* volatile*)&ws->zpar, zn[0], zn[1], lx, ly, lz, hx, hy,
-                                  hz);
+              // (block indices clamped to the image's blocks, as the supports
+              // are clamped to the image)
+              auto blk = [](float v, int o, int n) { return min(max(((int)floorf(v) + o) >> 2, 0), (n - 1) >> 2); };
+              const int lx = blk(fminf(ax, qx), *(volatile int*)&r.Op[0], zn[0]);
+              const int ly = blk(fminf(ay, qy), *(volatile int*)&r.Op[1], zn[1]);
+              const int lz = blk(fminf(az, qz), *(volatile int*)&r.Op[2], zn[2]);
+              const int hx = blk(fmaxf(ax, qx), *(volatile int*)&r.Op[0], zn[0]);
+              const int hy = blk(fmaxf(ay, qy), *(volatile int*)&r.Op[1], zn[1]);
+              const int hz = blk(fmaxf(az, qz), *(volatile int*)&r.Op[2], zn[2]);
+              const int BY = (zn[1] + 3) >> 2, W = (((zn[0] + 3) >> 2) + 63) >> 6;
+              const unsigned long long* zp = *(const unsigned long long* volatile*)&ws->zpar;
+              for (int bz = lz; bz <= hz && skip; ++bz)
+                for (int by = ly; by <= hy && skip; ++by) skip = occ_blocks_clear(zp, BY, W, lx, hx, by, bz);
             }
             if (skip) xs = 0;
           }

@@ -35,6 +35,9 @@ struct DevProblem {
   // (bz * BY + by) * W + (bx >> 6) set when block (bx, by, bz) holds a
   // nonzero voxel; BX = ceil(nx / 4), BY = ceil(ny / 4), W = ceil(BX / 64)
   const unsigned long long* occ[2];
+  // the same bitmap dilated by one block: bit set when any of the 27 blocks
+  // around (and including) the block holds a nonzero voxel
+  const unsigned long long* occd[2];
   int n[2][3];
   double spd[2][3];
   float sp[2][3];
@@ -149,6 +152,8 @@ void launch_build_nzsat(const void* plain, int dtype, const int n[3], int* sat, 
 // zeroed by the launch.
 long occ_words(const int n[3]);
 void launch_build_occ(const void* plain, int dtype, const int n[3], unsigned long long* occ, cudaStream_t st);
+// occd (occ_words(n) words, zeroed by the launch) = occ dilated by one block.
+void launch_dilate_occ(const unsigned long long* occ, const int n[3], unsigned long long* occd, cudaStream_t st);
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st);
 void launch_refine(const double* coarse, int n_cand, const int m[3], double* fine, cudaStream_t st);
 void launch_link_check(const DevProblem* probs, const DevProblem& hp, const int* cands, int n_cand, int* out,

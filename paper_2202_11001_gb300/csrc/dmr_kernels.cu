@@ -167,6 +167,26 @@ __global__ void k_occ(const void* plain, int st, int nx, int ny, int nz, unsigne
   if (any) atomicOr(occ + ((long)bz * BY + by) * W + (bx >> 6), 1ull << (bx & 63));
 }
 
+// Dilation by one block: one thread per block ORs the 27 blocks around it.
+__global__ void k_occ_dilate(const unsigned long long* occ, int nx, int ny, int nz, unsigned long long* occd) {
+  const int BX = (nx + 3) >> 2, BY = (ny + 3) >> 2, BZ = (nz + 3) >> 2, W = (BX + 63) >> 6;
+  const long id = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (id >= (long)BX * BY * BZ) return;
+  const int bx = (int)(id % BX), by = (int)((id / BX) % BY), bz = (int)(id / ((long)BX * BY));
+  bool any = false;
+  for (int z = max(bz - 1, 0); z <= min(bz + 1, BZ - 1) && !any; ++z)
+    for (int y = max(by - 1, 0); y <= min(by + 1, BY - 1) && !any; ++y)
+      for (int x = max(bx - 1, 0); x <= min(bx + 1, BX - 1) && !any; ++x)
+        any = (occ[((long)z * BY + y) * W + (x >> 6)] >> (x & 63)) & 1ull;
+  if (any) atomicOr(occd + ((long)bz * BY + by) * W + (bx >> 6), 1ull << (bx & 63));
+}
+
+void launch_dilate_occ(const unsigned long long* occ, const int n[3], unsigned long long* occd, cudaStream_t st) {
+  const long blocks = (long)((n[0] + 3) >> 2) * ((n[1] + 3) >> 2) * ((n[2] + 3) >> 2);
+  cudaMemsetAsync(occd, 0, sizeof(unsigned long long) * occ_words(n), st);
+  k_occ_dilate<<<(unsigned)((blocks + 127) / 128), 128, 0, st>>>(occ, n[0], n[1], n[2], occd);
+}
+
 long occ_words(const int n[3]) {
   const long BX = (n[0] + 3) >> 2, BY = (n[1] + 3) >> 2, BZ = (n[2] + 3) >> 2;
   return BY * BZ * ((BX + 63) >> 6);
