@@ -47,9 +47,10 @@ UNIT = "voxel-samples/s"
 ALG_OPS_PER_SAMPLE = 37
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one fast raster-pass launch (one wave of the
-# generation), from the ncu capture of the current kernel summarised under
+# generation, the mean over the 4 waves), from the full-size ncu capture of
+# the current kernel (1-pass metrics, caches not flushed) summarised under
 # profiles/, per (workload, storage); None for workloads without one.
-FAST_PASS_DRAM_BYTES = {}
+FAST_PASS_DRAM_BYTES = {("batch64", "f32"): 23.94e9, ("ct", "f32"): 2.498e9, ("ellipsoid64", "f32"): 5.3e6}
 
 
 def reduce_over_ranks(total_s, samples, dist, device):
@@ -316,6 +317,7 @@ def run_batch(args):
                 "counted_samples_per_step": counted_step, "executed_samples_per_step": executed_step,
                 "executed_frac": executed_step / max(counted_step, 1.0),
                 "executed_samples_per_s_raster": executed_step / raster_s,
+                "frac_on_counted_samples": counted_step * ALG_OPS_PER_SAMPLE / raster_s / 1e12 / alu_peak,
                 "touched_bytes_frac_of_hbm": value * 2 * bpv / 1e9 / hbm,
                 "touched_bytes_frac_of_hbm_executed": executed_step / (total_s / args.steps) * 2 * bpv / 1e9 / hbm,
                 "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind}
