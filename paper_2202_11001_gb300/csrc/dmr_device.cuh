@@ -157,7 +157,10 @@ static __device__ __forceinline__ void slice_yrange(const ItemRec& r, float zr, 
       if ((zi - zr) * (zj - zr) <= 0.f) {
         float y;
         if (zj != zi) {
-          float tq = (zr - zi) / (zj - zi);
+          // the range only needs to contain the rows (the caller widens it
+          // by a slack of 1/256 + 1e-5 |y|), so an approximate quotient
+          // (a few ulp) serves
+          float tq = __fdividef(zr - zi, zj - zi);
           tq = fminf(fmaxf(tq, 0.f), 1.f);
           y = fmaf(tq, yj - yi, yi);
           ylo = fminf(ylo, y);
@@ -457,6 +460,7 @@ struct WarpSmem {
   int zn[3];
   int zon;
   unsigned execd;  // samples of the current item mapped and sampled so far
+  int pend;        // fast pass: the second item of lane 0's last claimed pair, or -1
   // loop state parked here while the voxel loop runs (it holds no registers
   // there): per slice lane the first row index and first y of its slice, the
   // slice group, the batch, the rows of the group, the own image's nx and ny
@@ -602,6 +606,9 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
   __shared__ int s_cov[WARPS];
   const bool cta_mode = !FAST && WARPS > 1 && *(volatile unsigned*)(b.work + 1) < gridDim.x * (unsigned)WARPS;
   const int rstep = cta_mode ? 32 * WARPS : 32;
+  // fast pass: lane 0 claims items two at a time (one atomic per pair); the
+  // second waits in shared memory
+  if (FAST && lane == 0) ws->pend = -1;
   for (;;) {
     int item = 0;
     if (cta_mode) {
@@ -614,7 +621,14 @@ __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM
     } else {
       if (lane == 0) {
         if constexpr (FAST) {
-          item = (int)atomicAdd(b.work, 1u);
+          const int pend = *(volatile int*)&ws->pend;
+          if (pend >= 0) {
+            item = pend;
+            ws->pend = -1;
+          } else {
+            item = (int)atomicAdd(b.work, 2u);
+            ws->pend = item + 1;
+          }
         } else {
           const unsigned w = atomicAdd(b.work + 2, 1u);
           item = w < *(volatile unsigned*)(b.work + 1) ? b.slow[w] : n_items;
