@@ -589,7 +589,7 @@ enum { CF_ANY0 = 1, CF_ALL0 = 2, CF_NB_ALL0 = 4, CF_NB_NONE0 = 8, CF_NEAR = 16 }
 template <int ST, int WARPS, int VPL, bool FAST>
 __global__ void __launch_bounds__(WARPS * 32, (FAST && DMR_RASTER_THREADS_PER_SM / (WARPS * 32) > 0
                                                     ? DMR_RASTER_THREADS_PER_SM / (WARPS * 32)
-                                                    : (FAST ? 1 : 4)))
+                                                    : (FAST ? 1 : 6)))
     k_raster(const DevProblem* __restrict__ probs, Batch b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem* ws = (WarpSmem*)smem_raw + (threadIdx.x >> 5);
