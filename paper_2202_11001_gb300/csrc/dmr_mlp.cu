@@ -179,16 +179,28 @@ __device__ void stage_weights(unsigned char* dst, const __nv_bfloat16* W, int R,
 // Fused forward.  X [n][256] BF16; out [n][6] FP32 = (mean, log-variance).
 // Optional saves for training: Z [3][n][128] FP32 pre-activations and
 // H [3][n][128] BF16 activations.
+//
+// Two 128-row tiles are in flight per CTA: warps 0-7 (group 0) and 8-15
+// (group 1) each run their own tiles through the four layers, so the tensor
+// core multiplies one group's layer while the other group's warps run their
+// bias + GELU epilogue.  Each group owns a 32 KB operand buffer (128 rows x
+// K = 128 BF16) and 128 TMEM columns; layer 1's input (K = 256) is streamed
+// through the buffer in two K halves.  The weights (132 KB) stay resident.
 struct FwdSmem {
   static constexpr uint32_t W1 = 0, W2 = W1 + kHid * kIn * 2, W3 = W2 + kHid * kHid * 2, W4 = W3 + kHid * kHid * 2,
-                            ACT = W4 + kOutP * kHid * 2, BIAS = ACT + 128 * kIn * 2,
-                            MBAR = BIAS + (3 * kHid + kOutP) * 4, SLOT = MBAR + 8, TOTAL = SLOT + 8;
+                            ACT = W4 + kOutP * kHid * 2,               // 2 x 32 KB, one per group
+                            BIAS = ACT + 2 * 128 * kHid * 2, MBAR = BIAS + (3 * kHid + kOutP) * 4,
+                            SLOT = MBAR + 16, TOTAL = SLOT + 16;
 };
 
-// 16 warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and
-// accumulator columns 32 (w / 4) .. + 31, so the bias + GELU epilogue of a
-// 128 x 128 layer is spread over the whole CTA.
+// 16 warps = two groups of 8; in a group, warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (its rows) and accumulator columns 64 (w / 4) .. + 63.
 constexpr int kFwdThreads = 512;
+constexpr int kGroupThreads = 256;
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
 
 __global__ void __launch_bounds__(kFwdThreads, 1)
     k_mlp_forward(const __nv_bfloat16* __restrict__ X, int n, const __nv_bfloat16* __restrict__ Wb,
@@ -196,11 +208,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                   __nv_bfloat16* __restrict__ Hs, int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + FwdSmem::MBAR);
+  const int g = warp >> 3, gt = tid & (kGroupThreads - 1), wl = warp & 7;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + FwdSmem::MBAR) + g;
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + FwdSmem::SLOT);
   float* bias = reinterpret_cast<float*>(sm + FwdSmem::BIAS);
-  if (warp == 0) tmem_alloc(slot, 128);
-  if (tid == 0) mbar_init(mbar, 1);
+  if (warp == 0) tmem_alloc(slot, 256);
+  if (gt == 0) mbar_init(mbar, 1);
   stage_weights(sm + FwdSmem::W1, Wb + kOffW1, kHid, kIn);
   stage_weights(sm + FwdSmem::W2, Wb + kOffW2, kHid, kHid);
   stage_weights(sm + FwdSmem::W3, Wb + kOffW3, kHid, kHid);
@@ -211,69 +224,62 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     bias[2 * kHid + i] = P[kOffB3 + i];
   }
   if (tid < kOutP) bias[3 * kHid + tid] = P[kOffB4 + tid];
+  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tbase = *slot;
-  const uint32_t sAct = smem_u32(sm + FwdSmem::ACT);
+  const uint32_t tcol = *slot + 128u * (uint32_t)g;  // this group's accumulator columns
+  unsigned char* act = sm + FwdSmem::ACT + (uint32_t)g * (128 * kHid * 2);
+  const uint32_t sAct = smem_u32(act);
   const uint32_t sW[4] = {smem_u32(sm + FwdSmem::W1), smem_u32(sm + FwdSmem::W2), smem_u32(sm + FwdSmem::W3),
                           smem_u32(sm + FwdSmem::W4)};
-  const int quarter = warp & 3, cgrp = warp >> 2;
-  const uint32_t lane_base = tbase + ((uint32_t)(32 * quarter) << 16);
+  const int quarter = wl & 3, cgrp = wl >> 2;
+  const uint32_t lane_base = tcol + ((uint32_t)(32 * quarter) << 16);
   uint32_t phase = 0;
   bool ok = true;
   const int tiles = (n + 127) / 128;
-  // Input tile staging, asynchronous and in two row halves: in the K = 256
-  // layout rows 64..127 occupy bytes 32K..64K of ACT, which layers 2..4 (K =
-  // 128 activations, bytes 0..32K) leave free, and rows 0..63 are free again
-  // once layer 4's MMA has read the layer-3 activations; so the next tile's
-  // halves load while this tile's layers run.  Rows beyond n are zero.
-  auto stage_half = [&](int t, int half) {
-    const int m0 = t * 128;
-    for (int e = tid; e < 64 * (kIn / 8); e += kFwdThreads) {
-      const int r = 64 * half + e / (kIn / 8), c = e % (kIn / 8);
-      const bool valid = m0 + r < n;
-      cp_async16(sAct + kmaj_off(r, c * 8, kIn), valid ? (const void*)(X + (size_t)(m0 + r) * kIn + c * 8) : (const void*)X,
-                 valid);
-    }
-    cp_async_commit();
-  };
-  if ((int)blockIdx.x < tiles) {
-    stage_half(blockIdx.x, 0);
-    stage_half(blockIdx.x, 1);
-  }
-  for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-    const int m0 = tile * 128;
-    const int next = tile + gridDim.x;
-    cp_async_wait_all();
-    for (int layer = 0; layer < 4 && ok; ++layer) {
-      const int K = layer == 0 ? kIn : kHid;
-      const int N = layer == 3 ? kOutP : kHid;
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-        for (int s = 0; s < K / 16; ++s)
-          mma_bf16(tbase, sdesc(sAct + 256u * s, 128u, sbo), sdesc(sW[layer] + 256u * s, 128u, sbo),
-                   idesc_bf16(128, N), s > 0 ? 1u : 0u);
-        mma_commit(mbar);
-      }
-      bool w = mbar_wait(mbar, phase);
-      phase ^= 1u;
-      ok = __syncthreads_and(w) != 0;
-      if (!ok) break;
+  // the MMAs of one layer (or one K half of layer 1) from this group's
+  // buffer, then wait for them; false when the wait gave up
+  auto run_mma = [&](int layer, int s0, uint32_t bsbo, int N, bool accumulate_first) -> bool {
+    fence_async_smem();
+    tc_fence_before();
+    group_sync(g);
+    if (gt == 0) {
       tc_fence_after();
-      // the MMA has read its A operand: refill the half the next layers leave free
-      if (next < tiles && layer == 0) stage_half(next, 1);
-      if (next < tiles && layer == 3) stage_half(next, 0);
-      const int row = 32 * quarter + lane;
-      const int grow = m0 + row;
+      for (int s = 0; s < 8; ++s)
+        mma_bf16(tcol, sdesc(sAct + 256u * s, 128u, 2048u), sdesc(sW[layer] + 256u * (s0 + s), 128u, bsbo),
+                 idesc_bf16(128, N), (accumulate_first || s > 0) ? 1u : 0u);
+      mma_commit(mbar);
+    }
+    const bool w = mbar_wait(mbar, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    return w;
+  };
+  for (int tile = blockIdx.x + g * gridDim.x; tile < tiles && ok; tile += 2 * gridDim.x) {
+    const int m0 = tile * 128;
+    // layer 1: the input in two K halves of 128 columns
+    for (int h = 0; h < 2 && ok; ++h) {
+      for (int e = gt; e < 128 * (kHid / 8); e += kGroupThreads) {
+        const int r = e / (kHid / 8), c = e % (kHid / 8);
+        const bool valid = m0 + r < n;
+        cp_async16(sAct + kmaj_off(r, c * 8, kHid),
+                   valid ? (const void*)(X + (size_t)(m0 + r) * kIn + kHid * h + c * 8) : (const void*)X, valid);
+      }
+      cp_async_commit();
+      cp_async_wait_all();
+      ok = run_mma(0, 8 * h, (kIn / 8) * 128u, kHid, h > 0);
+    }
+    const int row = 32 * quarter + lane;
+    const int grow = m0 + row;
+    for (int layer = 0; layer < 4 && ok; ++layer) {
+      if (layer > 0) ok = run_mma(layer, 0, (kHid / 8) * 128u, layer == 3 ? kOutP : kHid, false);
+      if (!ok) break;
       if (layer < 3) {
-        // bias + GELU -> next layer's A operand (K = 128) in shared memory
-        {
-          const int c0 = 32 * cgrp;
+        // bias + GELU -> the next layer's operand in this group's buffer
+        // (the MMAs that read it have completed)
+        for (int half = 0; half < 2; ++half) {
+          const int c0 = 64 * cgrp + 32 * half;
           float v[32];
           tmem_ld32(lane_base + (uint32_t)c0, v);
 #pragma unroll
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           for (int q = 0; q < 4; ++q) {
             uint4 pk = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
                                   pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-            *reinterpret_cast<uint4*>(sm + FwdSmem::ACT + kmaj_off(row, c0 + 8 * q, kHid)) = pk;
+            *reinterpret_cast<uint4*>(act + kmaj_off(row, c0 + 8 * q, kHid)) = pk;
             if (Hs && grow < n)
               *reinterpret_cast<uint4*>(Hs + ((size_t)layer * n + grow) * kHid + c0 + 8 * q) = pk;
           }
@@ -297,11 +303,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         if (grow < n)
           for (int j = 0; j < kOut; ++j) out[(size_t)grow * kOut + j] = v[j] + bias[3 * kHid + j];
       }
-      tc_fence_before();
     }
+    // the next tile's input overwrites the buffer and the accumulator: every
+    // warp of the group is done with both
+    tc_fence_before();
+    group_sync(g);
   }
   if (!ok) {
-    if (tid == 0) atomicExch(err, kErrTimeout);
+    if (gt == 0) atomicExch(err, kErrTimeout);
     (void)mbar_wait(mbar, phase ^ 1u);  // give an outstanding commit one more bounded chance
   }
   cp_async_wait_all();  // no copy in flight when the CTA leaves
@@ -309,7 +318,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tbase, 128);
+    tmem_dealloc(*slot, 256);
   }
 }
 
@@ -671,7 +680,9 @@ void launch_forward(dmr_mlp* M, const __nv_bfloat16* X, int n, float* out, float
     once = true;
   }
   int tiles = (n + 127) / 128;
-  int grid = std::min(tiles, M->n_sm);
+  // two tiles in flight per CTA once there are more tiles than SMs; with
+  // fewer (training batches) one tile per CTA, on more SMs
+  int grid = tiles <= M->n_sm ? tiles : std::min((tiles + 1) / 2, M->n_sm);
   k_mlp_forward<<<grid, kFwdThreads, FwdSmem::TOTAL, M->st>>>(X, n, M->Wb, M->P, out, Zs, Hs, M->err);
 }
 
