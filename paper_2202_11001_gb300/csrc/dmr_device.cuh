@@ -29,6 +29,35 @@ static __device__ __forceinline__ double dot3d(const double a[3], const double b
   return dadd(dmul(a[0], b[0]), dadd(dmul(a[1], b[1]), dmul(a[2], b[2])));
 }
 
+// Conversions that keep the FP64 pipe free: on GB300 double arithmetic and
+// double <-> float / int conversions all issue at under 2 operations per SM
+// clock (FP32 arithmetic: over 100), so a kernel bound by its FP64 work
+// converts in integer arithmetic instead.  d2f: IEEE-754 binary64 -> binary32
+// with round-to-nearest-even, written out for results in the normal binary32
+// range (the 23 leading fraction bits, the 29 dropped bits decide the
+// rounding, a carry runs into the exponent and past the largest finite value
+// to infinity); zeros, subnormal results, infinities and NaN take the
+// hardware conversion.
+static __device__ __forceinline__ float d2f(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex - 897u > 253u) return __double2float_rn(x);
+  unsigned f = ((ex - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned r = lo & 0x1fffffffu;
+  f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | f);
+}
+// i2d: the exact binary64 value of a 32-bit integer (leading one found by
+// counting leading zeros, the bits below it become the fraction).
+static __device__ __forceinline__ double i2d(int v) {
+  if (v == 0) return 0.0;
+  const unsigned s = v < 0 ? 0x80000000u : 0u;
+  const unsigned a = v < 0 ? 0u - (unsigned)v : (unsigned)v;
+  const int lz = __clz(a);
+  const unsigned fr = a << lz << 1;  // two shifts: lz + 1 may be 32
+  return __hiloint2double((int)(s | ((unsigned)(1054 - lz) << 20) | (fr >> 12)), (int)(fr << 20));
+}
+
 // Exact face predicate: canonical face (a,b,c) with inward sign s; p on the
 // inner side, or on the plane and the signed normal's first nonzero
 // component in (z, y, x) order is positive.

@@ -231,7 +231,8 @@ __device__ __forceinline__ double pick4d(const double (&v)[4][3], int i, int a) 
 
 
 // One thread per (trial, tet): fold count, deformation, and the two
-// direction records (Sec. 2.3.1-2.3.4).
+// direction records (Sec. 2.3.1-2.3.4).  Its roundings of FP64 values to FP32 use d2f
+// (integer arithmetic), which leaves the FP64 pipe to the FP64 arithmetic.
 // k_setup writes records as 16-byte words; the layout it relies on
 static_assert(offsetof(ItemRec, b0) == 16 && offsetof(ItemRec, b1) == 32 && offsetof(ItemRec, O) == 48 &&
                   offsetof(ItemRec, Op) == 64 && offsetof(ItemRec, cbase) == 80 && offsetof(ItemRec, vr) % 16 == 0 &&
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
   for (int i = 0; i < 3; ++i)
     for (int a = 0; a < 3; ++a) {
       Dm[i][a] = dsub(e[1][i][a], e[0][i][a]);
-      Dmf[i][a] = (float)Dm[i][a];
+      Dmf[i][a] = d2f(Dm[i][a]);
     }
 
   // deformation (FP32 from FP64 edge vectors and their differences)
@@ -302,8 +303,8 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     float es[3][3], dd[3][3];
     for (int i = 0; i < 3; ++i)
       for (int a = 0; a < 3; ++a) {
-        es[i][a] = (float)e[0][i][a];
-        dd[i][a] = (float)Dm[i][a];
+        es[i][a] = d2f(e[0][i][a]);
+        dd[i][a] = Dmf[i][a];
       }
     // 6 edges + 4 spokes as combinations of the 3 base edges (v0 at 0):
     // positions 0, e1, e2, e3.  Length change via (lt^2 - ls^2)/(lt + ls).
@@ -353,10 +354,10 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
   for (int mesh = 0; mesh < 2; ++mesh) {
     mfin[mesh] = true;
     for (int a = 0; a < 3; ++a) {
-      mlo[mesh][a] = mhi[mesh][a] = (float)X[mesh][0][a];
+      mlo[mesh][a] = mhi[mesh][a] = d2f(X[mesh][0][a]);
       mfin[mesh] = mfin[mesh] && isfinite(mlo[mesh][a]);
       for (int i = 1; i < 4; ++i) {
-        const float v = (float)X[mesh][i][a];
+        const float v = d2f(X[mesh][i][a]);
         mlo[mesh][a] = fminf(mlo[mesh][a], v);
         mhi[mesh][a] = fmaxf(mhi[mesh][a], v);
         mfin[mesh] = mfin[mesh] && isfinite(v);
@@ -441,11 +442,11 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     float G[3][4];
     float gabs = 0.f;
     {
-      const float invf = (d == 0 ? 1.0f : -1.0f) / (float)vol6[d];
+      const float invf = (d == 0 ? 1.0f : -1.0f) / d2f(vol6[d]);
       const float ainv = fabsf(invf);
       float rf[3][3];
       for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) rf[i][j] = (float)rr[i][j];
+        for (int j = 0; j < 3; ++j) rf[i][j] = d2f(rr[i][j]);
       for (int c = 0; c < 3; ++c)
         for (int j = 0; j < 3; ++j) {
           G[c][j] = fmaf(Dmf[0][c], rf[0][j], fmaf(Dmf[1][c], rf[1][j], Dmf[2][c] * rf[2][j])) * invf;
@@ -505,8 +506,8 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     for (int i = 0; i < 4; ++i) {
       float vr[3];
       for (int a = 0; a < 3; ++a) {
-        vd[i][a] = dsub(own[i][a], (double)O[a]);
-        vr[a] = (float)vd[i][a];
+        vd[i][a] = dsub(own[i][a], i2d(O[a]));
+        vr[a] = d2f(vd[i][a]);
         V = fmaxf(V, fabsf(vr[a]));
       }
       *reinterpret_cast<float4*>(&R.vr[i][0]) = make_float4(vr[0], vr[1], vr[2], 0.f);
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       const double ny = opp == 0 ? N0[1] : opp == 1 ? rr[0][1] : opp == 2 ? rr[1][1] : rr[2][1];
       const double nz = opp == 0 ? N0[2] : opp == 1 ? rr[0][2] : opp == 2 ? rr[1][2] : rr[2][2];
       const double Bd = -fma(nx, pick4d(vd, ia, 0), fma(ny, pick4d(vd, ia, 1), nz * pick4d(vd, ia, 2)));
-      const float Ax = (float)nx, Ay = (float)ny, Az = (float)nz, Bp = (float)Bd;
+      const float Ax = d2f(nx), Ay = d2f(ny), Az = d2f(nz), Bp = d2f(Bd);
       axf[f] = Ax;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
       const float mu = (5.0f / 16777216.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
@@ -559,11 +560,11 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     // eps M; the evaluation's ~7 eps M: inside the black-decision margin
     // 2^-19 M = 32 eps M
     float gmax = 0.f, kmax = 0.f;
-    const float oo0 = (float)dsub((double)O[0], own[0][0]), oo1 = (float)dsub((double)O[1], own[0][1]),
-                oo2 = (float)dsub((double)O[2], own[0][2]);
+    const float oo0 = d2f(dsub(i2d(O[0]), own[0][0])), oo1 = d2f(dsub(i2d(O[1]), own[0][1])),
+                oo2 = d2f(dsub(i2d(O[2]), own[0][2]));
     for (int c = 0; c < 3; ++c) {
       for (int j = 0; j < 3; ++j) gmax = fmaxf(gmax, fabsf(G[c][j]));
-      const float d0 = (float)dsub(par[0][c], own[0][c]);
+      const float d0 = d2f(dsub(par[0][c], own[0][c]));
       G[c][3] = ((float)(O[c] - Op[c]) + d0) + fmaf(G[c][0], oo0, fmaf(G[c][1], oo1, G[c][2] * oo2));
       kmax = fmaxf(kmax, fabsf(G[c][3]));
       *reinterpret_cast<float4*>(&R.G[c][0]) = make_float4(G[c][0], G[c][1], G[c][2], G[c][3]);
