@@ -230,19 +230,26 @@ __device__ __forceinline__ double pick4d(const double (&v)[4][3], int i, int a) 
 
 
 
-// One thread per (trial, tet): fold count, deformation, and the two
-// direction records (Sec. 2.3.1-2.3.4).  Its roundings of FP64 values to FP32 use d2f
-// (integer arithmetic), which leaves the FP64 pipe to the FP64 arithmetic.
+// Two threads per (trial, tet), adjacent lanes, thread d for mesh d and
+// direction d (Sec. 2.3.1-2.3.4): each loads its mesh's vertices, forms its
+// edge vectors, volume and FP32 box, takes the pair's edges, first vertex
+// and box by shuffles, and writes its direction's record (its vertices also
+// go to the pair's record as the partner's); thread 0 adds the fold counts
+// and computes the deformation.  Its roundings of FP64 values to FP32 use
+// d2f (integer arithmetic), which leaves the FP64 pipe to the FP64
+// arithmetic.
 // k_setup writes records as 16-byte words; the layout it relies on
 static_assert(offsetof(ItemRec, b0) == 16 && offsetof(ItemRec, b1) == 32 && offsetof(ItemRec, O) == 48 &&
                   offsetof(ItemRec, Op) == 64 && offsetof(ItemRec, cbase) == 80 && offsetof(ItemRec, vr) % 16 == 0 &&
                   offsetof(ItemRec, X) % 16 == 0 && offsetof(ItemRec, XP) % 16 == 0 && sizeof(ItemRec) % 16 == 0,
               "ItemRec layout");
 
-__global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch b) {
-  int tt = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tt == 0 && b.work) b.work[0] = b.work[1] = b.work[2] = 0u;
-  if (tt >= b.n_tt) return;
+__global__ void __launch_bounds__(128, 4) k_setup(const DevProblem* probs, Batch b) {
+  const long gi = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi == 0 && b.work) b.work[0] = b.work[1] = b.work[2] = 0u;
+  const int tt = (int)(gi >> 1), d = (int)(gi & 1);
+  if (tt >= b.n_tt) return;  // both lanes of a pair (blocks hold whole pairs)
+  const unsigned pair = 3u << (threadIdx.x & 30);
   int k = b.tt_trial[tt];
   int t = b.tt_tet[tt];
   const int pi = b.tr_prob ? b.tr_prob[k] : 0;
@@ -251,59 +258,55 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
   int4 tv = pr.tet[t];
   int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   uint32_t slots = b.tt_slot ? b.tt_slot[tt] : 0u;
-  double X[2][4][3];
-  for (int mesh = 0; mesh < 2; ++mesh)
-    for (int i = 0; i < 4; ++i)
-      for (int a = 0; a < 3; ++a) X[mesh][i][a] = vcoord(pr, b, k, cand, slots, i, vid[i], mesh, a);
+  double own[4][3];
+  for (int i = 0; i < 4; ++i)
+    for (int a = 0; a < 3; ++a) own[i][a] = vcoord(pr, b, k, cand, slots, i, vid[i], d, a);
 
-  // edge vectors and fold (FP64, oracle expression order: the volume sign
-  // decides an integer)
-  double e[2][3][3];
-  for (int mesh = 0; mesh < 2; ++mesh)
-    for (int i = 0; i < 3; ++i)
-      for (int a = 0; a < 3; ++a) e[mesh][i][a] = dsub(X[mesh][i + 1][a], X[mesh][0][a]);
-  int fold = 0;
-  double vol6[2], r0[2][3];
-  for (int mesh = 0; mesh < 2; ++mesh) {
-    cross3d(e[mesh][1], e[mesh][2], r0[mesh]);
-    vol6[mesh] = dot3d(e[mesh][0], r0[mesh]);
-    if (!(vol6[mesh] > 0 && isfinite(vol6[mesh]))) ++fold;
-  }
+  // edge vectors and this mesh's fold (FP64, oracle expression order: the
+  // volume sign decides an integer)
+  double eo[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a) eo[i][a] = dsub(own[i + 1][a], own[0][a]);
+  double r0[3];
+  cross3d(eo[1], eo[2], r0);
+  const double vol6 = dot3d(eo[0], r0);
+  int fold = (vol6 > 0 && isfinite(vol6)) ? 0 : 1;
   // fixed axes: the coordinate must equal its border value exactly; both
   // sides are never 0, so equality is equality of the bit patterns (a NaN
   // differs from every border value either way)
   for (int i = 0; i < 4; ++i) {
     uint8_t fm = pr.fixmask[vid[i]];
     if (!fm) continue;
-    for (int mesh = 0; mesh < 2; ++mesh) {
-      int bad = 0;
-      for (int a = 0; a < 3; ++a)
-        if ((fm >> a) & 1) {
-          double rv = ((fm >> (3 + a)) & 1) ? (double)pr.n[mesh][a] - 0.5 : -0.5;
-          if (__double_as_longlong(X[mesh][i][a]) != __double_as_longlong(rv)) bad = 1;
-        }
-      fold += bad;
-    }
+    int bad = 0;
+    for (int a = 0; a < 3; ++a)
+      if ((fm >> a) & 1) {
+        double rv = ((fm >> (3 + a)) & 1) ? (double)pr.n[d][a] - 0.5 : -0.5;
+        if (__double_as_longlong(own[i][a]) != __double_as_longlong(rv)) bad = 1;
+      }
+    fold += bad;
   }
-  b.o_fold[tt] = fold;
+  fold += __shfl_xor_sync(pair, fold, 1);
+  if (d == 0) b.o_fold[tt] = fold;
 
   // edge differences target - source (direction 0's D; direction 1 uses -D,
-  // exactly, since a - b = -(b - a) in round-to-nearest)
-  double Dm[3][3];
+  // exactly, since a - b = -(b - a) in round-to-nearest), from the pair's
+  // edges
   float Dmf[3][3];
   for (int i = 0; i < 3; ++i)
     for (int a = 0; a < 3; ++a) {
-      Dm[i][a] = dsub(e[1][i][a], e[0][i][a]);
-      Dmf[i][a] = d2f(Dm[i][a]);
+      const double ep = __shfl_xor_sync(pair, eo[i][a], 1);
+      Dmf[i][a] = d2f(d == 0 ? dsub(ep, eo[i][a]) : dsub(eo[i][a], ep));
     }
+  double par0[3];
+  for (int a = 0; a < 3; ++a) par0[a] = __shfl_xor_sync(pair, own[0][a], 1);
 
   // deformation (FP32 from FP64 edge vectors and their differences)
   double def = 0.0;
-  if (pr.model == 0) {
+  if (d == 0 && pr.model == 0) {
     float es[3][3], dd[3][3];
     for (int i = 0; i < 3; ++i)
       for (int a = 0; a < 3; ++a) {
-        es[i][a] = d2f(e[0][i][a]);
+        es[i][a] = d2f(eo[i][a]);
         dd[i][a] = Dmf[i][a];
       }
     // 6 edges + 4 spokes as combinations of the 3 base edges (v0 at 0):
@@ -346,89 +349,90 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     def = (double)acc;
   }
 
-  // FP32 bounding boxes of both meshes' vertices (rounding is monotone, so
-  // ceil/floor of the rounded extremes give a superset of the voxels a tet
-  // can hold); finiteness of every rounded coordinate
-  float mlo[2][3], mhi[2][3];
-  bool mfin[2];
-  for (int mesh = 0; mesh < 2; ++mesh) {
-    mfin[mesh] = true;
-    for (int a = 0; a < 3; ++a) {
-      mlo[mesh][a] = mhi[mesh][a] = d2f(X[mesh][0][a]);
-      mfin[mesh] = mfin[mesh] && isfinite(mlo[mesh][a]);
-      for (int i = 1; i < 4; ++i) {
-        const float v = d2f(X[mesh][i][a]);
-        mlo[mesh][a] = fminf(mlo[mesh][a], v);
-        mhi[mesh][a] = fmaxf(mhi[mesh][a], v);
-        mfin[mesh] = mfin[mesh] && isfinite(v);
-      }
+  // FP32 bounding boxes of the own vertices and, from the pair, of the
+  // partner vertices (rounding is monotone, so ceil/floor of the rounded
+  // extremes give a superset of the voxels a tet can hold); finiteness of
+  // every rounded coordinate
+  float olo[3], ohi[3], plo_[3], phi_[3];
+  bool ofin = true;
+  for (int a = 0; a < 3; ++a) {
+    olo[a] = ohi[a] = d2f(own[0][a]);
+    ofin = ofin && isfinite(olo[a]);
+    for (int i = 1; i < 4; ++i) {
+      const float v = d2f(own[i][a]);
+      olo[a] = fminf(olo[a], v);
+      ohi[a] = fmaxf(ohi[a], v);
+      ofin = ofin && isfinite(v);
     }
   }
+  for (int a = 0; a < 3; ++a) {
+    plo_[a] = __shfl_xor_sync(pair, olo[a], 1);
+    phi_[a] = __shfl_xor_sync(pair, ohi[a], 1);
+  }
+  const bool pfin = __shfl_xor_sync(pair, (int)ofin, 1) != 0;
 
-  // Zero-region bits of each direction (ItemRec::flags bit2 / bit3, kept
+  // Zero-region bits of the direction (ItemRec::flags bit2 / bit3, kept
   // below only where the map is finite and small): no nonzero / no zero
   // partner voxel within 2 voxels of the partner tet's box (clamped to the
   // image).  A voxel inside the own tet maps into the partner tet (the FP32
   // map within a small fraction of a voxel of it, as for bit1), so its FP32
   // cell and its exact support, clamped, lie in that region: with no nonzero
   // voxel there the sample is 0 and black, with no 0 it is not black.
-  int zbits[2] = {0, 0};
-#pragma unroll
-  for (int d = 0; d < 2; ++d) {
+  int zbits = 0;
+  {
     const int* np = pr.n[1 - d];
-    if (mfin[1 - d] && pr.nzsat[1 - d]) {
+    if (pfin && pr.nzsat[1 - d]) {
       int q0[3], q1[3];
       for (int a = 0; a < 3; ++a) {
         const float hiv = (float)(np[a] - 1);
-        q0[a] = (int)fminf(fmaxf(floorf(mlo[1 - d][a]) - 2.0f, 0.0f), hiv);
-        q1[a] = (int)fminf(fmaxf(ceilf(mhi[1 - d][a]) + 2.0f, 0.0f), hiv);
+        q0[a] = (int)fminf(fmaxf(floorf(plo_[a]) - 2.0f, 0.0f), hiv);
+        q1[a] = (int)fminf(fmaxf(ceilf(phi_[a]) + 2.0f, 0.0f), hiv);
       }
       const long nzc = nz_in_box(pr.nzsat[1 - d], np, q0, q1);
       const long vol = (long)(q1[0] - q0[0] + 1) * (q1[1] - q0[1] + 1) * (q1[2] - q0[2] + 1);
-      zbits[d] = (nzc == 0 ? 4 : 0) | (nzc == vol ? 8 : 0);
+      zbits = (nzc == 0 ? 4 : 0) | (nzc == vol ? 8 : 0);
       // bit4 (with bit2): the own image is 0 over the own tet's box too, so
       // every sample is 0 against 0 (d^2 = 0, black or not): only the
       // coverage is counted
       const int* no = pr.n[d];
-      if ((zbits[d] & 4) && mfin[d] && pr.nzsat[d]) {
+      if ((zbits & 4) && ofin && pr.nzsat[d]) {
         int o0[3], o1[3];
         bool empty = false;
         for (int a = 0; a < 3; ++a) {
-          o0[a] = (int)fminf(fmaxf(ceilf(mlo[d][a]), 0.0f), (float)(no[a] - 1));
-          o1[a] = (int)fminf(fmaxf(floorf(mhi[d][a]), 0.0f), (float)(no[a] - 1));
+          o0[a] = (int)fminf(fmaxf(ceilf(olo[a]), 0.0f), (float)(no[a] - 1));
+          o1[a] = (int)fminf(fmaxf(floorf(ohi[a]), 0.0f), (float)(no[a] - 1));
           empty = empty || o0[a] > o1[a];
         }
-        if (!empty && nz_in_box(pr.nzsat[d], no, o0, o1) == 0) zbits[d] |= 16;
+        if (!empty && nz_in_box(pr.nzsat[d], no, o0, o1) == 0) zbits |= 16;
       }
     }
   }
 
-  // the two directions (unrolled so the vertex arrays stay in registers);
-  // each record is assembled in registers and written with 16-byte stores
-#pragma unroll
-  for (int d = 0; d < 2; ++d) {
+  // the direction's record, assembled in registers and written with 16-byte
+  // stores
+  do {
     ItemRec& R = b.rec[2 * (size_t)tt + d];
-    const double(*own)[3] = X[d];
-    const double(*par)[3] = X[1 - d];
-    const double(*eo)[3] = e[d];
     const int* n = pr.n[d];
     const int* np = pr.n[1 - d];
-    int flags = (vol6[d] > 0 && isfinite(vol6[d])) ? 1 : 0;
+    int flags = (vol6 > 0 && isfinite(vol6)) ? 1 : 0;
     {
+      // this thread's mesh is the own mesh of its record and the partner
+      // mesh of the pair's record
       double2* xs = reinterpret_cast<double2*>(&R.X[0][0]);
-      double2* xp = reinterpret_cast<double2*>(&R.XP[0][0]);
+      double2* xp = reinterpret_cast<double2*>(&b.rec[2 * (size_t)tt + (1 - d)].XP[0][0]);
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
         const int i0 = (2 * q) / 3, a0 = (2 * q) % 3, i1 = (2 * q + 1) / 3, a1 = (2 * q + 1) % 3;
-        xs[q] = make_double2(own[i0][a0], own[i1][a1]);
-        xp[q] = make_double2(par[i0][a0], par[i1][a1]);
+        const double2 v = make_double2(own[i0][a0], own[i1][a1]);
+        xs[q] = v;
+        xp[q] = v;
       }
     }
     // adjugate rows of the own edge matrix (FP64, fused; they give the face
     // normals below and, rounded, the FP32 map; the decisions that need the
     // exact-order map rebuild it from X and XP); det = 6V_own
     double rr[3][3];
-    for (int j = 0; j < 3; ++j) rr[0][j] = r0[d][j];
+    for (int j = 0; j < 3; ++j) rr[0][j] = r0[j];
     rr[1][0] = fma(eo[2][1], eo[0][2], -eo[2][2] * eo[0][1]);
     rr[1][1] = fma(eo[2][2], eo[0][0], -eo[2][0] * eo[0][2]);
     rr[1][2] = fma(eo[2][0], eo[0][1], -eo[2][1] * eo[0][0]);
@@ -442,7 +446,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     float G[3][4];
     float gabs = 0.f;
     {
-      const float invf = (d == 0 ? 1.0f : -1.0f) / d2f(vol6[d]);
+      const float invf = (d == 0 ? 1.0f : -1.0f) / d2f(vol6);
       const float ainv = fabsf(invf);
       float rf[3][3];
       for (int i = 0; i < 3; ++i)
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
         }
     }
     // linear-elastic energy from the source->target map (direction 0)
-    if (d == 0 && pr.model == 1 && vol6[0] != 0.0 && isfinite(vol6[0])) {
+    if (d == 0 && pr.model == 1 && vol6 != 0.0 && isfinite(vol6)) {
       float H[3][3];
       for (int c = 0; c < 3; ++c)
         for (int j = 0; j < 3; ++j) {
@@ -477,14 +481,13 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       R4[0] = make_int4(0, pi, t, d);
       R4[1] = make_int4(1, 1, 1, 1);
       R4[2] = make_int4(0, 0, 0, 0);
-      continue;
+      break;
     }
     // bbox and origins
-    const float* lo = mlo[d];
-    const float* hi = mhi[d];
-    const float* plo = mlo[1 - d];
-    const float* phi = mhi[1 - d];
-    const bool pfin = mfin[1 - d];
+    const float* lo = olo;
+    const float* hi = ohi;
+    const float* plo = plo_;
+    const float* phi = phi_;
     int O[3], Op[3], B0[3], B1[3];
     int L = 1;
     for (int a = 0; a < 3; ++a) {
@@ -564,7 +567,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
                 oo2 = d2f(dsub(i2d(O[2]), own[0][2]));
     for (int c = 0; c < 3; ++c) {
       for (int j = 0; j < 3; ++j) gmax = fmaxf(gmax, fabsf(G[c][j]));
-      const float d0 = d2f(dsub(par[0][c], own[0][c]));
+      const float d0 = d2f(dsub(par0[c], own[0][c]));
       G[c][3] = ((float)(O[c] - Op[c]) + d0) + fmaf(G[c][0], oo0, fmaf(G[c][1], oo1, G[c][2] * oo2));
       kmax = fmaxf(kmax, fabsf(G[c][3]));
       *reinterpret_cast<float4*>(&R.G[c][0]) = make_float4(G[c][0], G[c][1], G[c][2], G[c][3]);
@@ -583,7 +586,7 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
       for (int a = 0; a < 3; ++a) in = in && plo[a] >= -0.75f && phi[a] <= (float)np[a] - 0.25f;
       if (flags && in) flags |= 2;
     }
-    if (flags && mapok) flags |= zbits[d] | 32;
+    if (flags && mapok) flags |= zbits | 32;
     R4[0] = make_int4(flags, pi, t, d);
     // gx: (1 + G00, G10, G20, black-decision margin delta = 2^-19 M)
     *reinterpret_cast<float4*>(&R.gx[0]) = make_float4(1.0f + G[0][0], G[1][0], G[2][0], M * (1.0f / 524288.0f));
@@ -598,8 +601,8 @@ __global__ void __launch_bounds__(128, 3) k_setup(const DevProblem* probs, Batch
     int forder, fshape;
     face_order(axf, forder, fshape);
     R4[5] = make_int4((int)base, forder, fshape, 0);
-  }
-  b.o_def[tt] = def;
+  } while (false);
+  if (d == 0) b.o_def[tt] = def;
 }
 
 // ------------------------------------------------------------ refinement
@@ -789,7 +792,7 @@ void launch_gather_deltas(const double* const* raw, const int* slot_q, const lon
 
 void launch_setup(const DevProblem* probs, const Batch& b, cudaStream_t st) {
   if (b.n_tt <= 0) return;
-  k_setup<<<(b.n_tt + 127) / 128, 128, 0, st>>>(probs, b);
+  k_setup<<<(unsigned)((2L * b.n_tt + 127) / 128), 128, 0, st>>>(probs, b);
 }
 
 // ------------------------------------------------------------ raster + sample
