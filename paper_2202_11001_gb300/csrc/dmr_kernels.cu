@@ -244,7 +244,7 @@ static_assert(offsetof(ItemRec, b0) == 16 && offsetof(ItemRec, b1) == 32 && offs
                   offsetof(ItemRec, X) % 16 == 0 && offsetof(ItemRec, XP) % 16 == 0 && sizeof(ItemRec) % 16 == 0,
               "ItemRec layout");
 
-__global__ void __launch_bounds__(128, 4) k_setup(const DevProblem* probs, Batch b) {
+__global__ void __launch_bounds__(128, 4) k_setup(const DevProblem* __restrict__ probs, Batch b) {
   const long gi = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi == 0 && b.work) b.work[0] = b.work[1] = b.work[2] = 0u;
   const int tt = (int)(gi >> 1), d = (int)(gi & 1);
