@@ -6,9 +6,11 @@
 // this is the one dense contraction of the path, so it runs as tcgen05.mma
 // (BF16 operands in shared memory, FP32 accumulators in tensor memory):
 //
-//  * k_mlp_forward  persistent, one 128-row tile at a time: the four layers
-//                   fused, weights resident in shared memory, activations
-//                   kept on chip (TMEM -> registers -> shared memory);
+//  * k_mlp_forward  persistent, two 128-row tiles in flight per CTA: the four
+//                   layers fused, weights resident in shared memory, the
+//                   input streamed by TMA through a ring of shared-memory
+//                   chunks, hidden activations kept in tensor memory (the
+//                   next layer's A operand);
 //  * k_gemm_tc      C (+)= op(A) op(B) for the backward pass (any strides,
 //                   transposes folded into the shared-memory staging);
 //  * small CUDA-core kernels for features, the loss gradient, GELU', bias
@@ -21,6 +23,7 @@
 // offset).  Every wait on an mbarrier is bounded; on a timeout the kernel
 // records an error code, waits once more (bounded), frees its tensor memory
 // and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -73,6 +76,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// D (+)= A B with A (M x K, BF16 pairs per 32-bit column, row m in lane m)
+// in tensor memory.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
@@ -136,6 +148,40 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// One mbarrier arrival that also expects `bytes` of asynchronous copies.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+// TMA: the box at (x, y, z) of a 3-D tensor map into shared memory,
+// completing on mbarrier m.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(m))
+      : "memory");
+}
+// TMA: the box at (x, y) of a 2-D tensor map into shared memory, completing
+// on mbarrier m.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(m))
+      : "memory");
+}
+
 // GELU in its tanh form (Hendrycks & Gimpel): 0.5 z (1 + tanh(c (z + a z^3))),
 // c = sqrt(2/pi), a = 0.044715; tanh from the hardware approximation, whose
 // error is below the BF16 rounding the activations receive.
@@ -159,13 +205,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Asynchronous 16-byte global -> shared copy (zero fill when !valid).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Load R x K BF16 weights [R][K] from global into the canonical layout.
 __device__ void stage_weights(unsigned char* dst, const __nv_bfloat16* W, int R, int K) {
   const int chunks = R * (K / 8);
@@ -176,22 +215,40 @@ __device__ void stage_weights(unsigned char* dst, const __nv_bfloat16* W, int R,
   }
 }
 
-// Fused forward.  X [n][256] BF16; out [n][6] FP32 = (mean, log-variance).
-// Optional saves for training: Z [3][n][128] FP32 pre-activations and
-// H [3][n][128] BF16 activations.
+// Fused forward.  X [n][256] BF16 (through the tensor map tmX); out [n][6]
+// FP32 = (mean, log-variance).  Optional saves for training: Z [3][n][128]
+// FP32 pre-activations and H [3][n][128] BF16 activations.
 //
 // Two 128-row tiles are in flight per CTA: warps 0-7 (group 0) and 8-15
-// (group 1) each run their own tiles through the four layers, so the tensor
+// (group 1) take the CTA's tiles alternately (its i-th tile, i = 0, 1, ...,
+// goes to group i % 2) and run them through the four layers, so the tensor
 // core multiplies one group's layer while the other group's warps run their
-// bias + GELU epilogue.  Each group owns a 32 KB operand buffer (128 rows x
-// K = 128 BF16) and 128 TMEM columns; layer 1's input (K = 256) is streamed
-// through the buffer in two K halves.  The weights (132 KB) stay resident.
+// bias + GELU epilogue.  Each group owns 256 TMEM columns: the FP32
+// accumulator (128) and the hidden activation as BF16 pairs (64), which the
+// epilogue stores there and the next layer's MMAs read as their A operand.
+// The input reaches shared memory by TMA in chunks of 128 rows x 32 K (8 KB,
+// 8 per tile; column group q of 8 columns at 2 KB q, row r at 16 r within
+// it: 8 x 8 core matrices 2 KB apart along K and 128 B apart along the
+// rows) through a ring of kRing slots: chunk j of tile i is number
+// 8 i + j, slot (8 i + j) % kRing, completing on that slot's mbarrier.  The
+// first kRing chunks are loaded up front; when a tile's layer-1 MMAs have
+// completed, its group loads the chunks kRing further on into the slots it
+// freed, so the next tiles' inputs arrive while this tile runs layers 2-4.
+// A tile's layer 1 starts only after the previous tile's layer 1 has
+// completed, so every slot mbarrier a group waits on is at most one phase
+// ahead of the last phase it completed (the parity wait is unambiguous).
+// The weights (132 KB) stay resident.
+constexpr int kRing = 11;
+constexpr int kChunkK = 32, kChunks = kIn / kChunkK;
+constexpr uint32_t kChunkBytes = 128u * kChunkK * 2u;
 struct FwdSmem {
   static constexpr uint32_t W1 = 0, W2 = W1 + kHid * kIn * 2, W3 = W2 + kHid * kHid * 2, W4 = W3 + kHid * kHid * 2,
-                            ACT = W4 + kOutP * kHid * 2,               // 2 x 32 KB, one per group
-                            BIAS = ACT + 2 * 128 * kHid * 2, MBAR = BIAS + (3 * kHid + kOutP) * 4,
-                            SLOT = MBAR + 16, TOTAL = SLOT + 16;
+                            RING = W4 + kOutP * kHid * 2, BIAS = RING + kRing * kChunkBytes,
+                            MBAR = BIAS + (3 * kHid + kOutP) * 4,  // acc[2], full[kRing]
+                            FLAG = MBAR + 8 * (2 + kRing),          // layer-1 tiles done, highest chunk issued
+                            SLOT = FLAG + 8, TOTAL = SLOT + 16;
 };
+static_assert(FwdSmem::RING % 1024 == 0 && FwdSmem::MBAR % 8 == 0, "forward shared-memory layout");
 
 // 16 warps = two groups of 8; in a group, warp w reads TMEM lanes
 // 32 (w % 4) .. + 31 (its rows) and accumulator columns 64 (w / 4) .. + 63.
@@ -201,19 +258,59 @@ constexpr int kGroupThreads = 256;
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
 }
+// Group barrier that returns the AND of `pred` over the group's threads.
+__device__ __forceinline__ bool group_all(int g, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "barrier.cta.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(1 + g), "r"(kGroupThreads)
+      : "memory");
+  return r != 0;
+}
 
 __global__ void __launch_bounds__(kFwdThreads, 1)
-    k_mlp_forward(const __nv_bfloat16* __restrict__ X, int n, const __nv_bfloat16* __restrict__ Wb,
+    k_mlp_forward(const __grid_constant__ CUtensorMap tmX, int map3d, int n, const __nv_bfloat16* __restrict__ Wb,
                   const float* __restrict__ P, float* __restrict__ out, float* __restrict__ Zs,
                   __nv_bfloat16* __restrict__ Hs, int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = warp >> 3, gt = tid & (kGroupThreads - 1), wl = warp & 7;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + FwdSmem::MBAR) + g;
+  uint64_t* accb = reinterpret_cast<uint64_t*>(sm + FwdSmem::MBAR) + g;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + FwdSmem::MBAR) + 2;
+  volatile int* l1done = reinterpret_cast<volatile int*>(sm + FwdSmem::FLAG);
+  int* issued = reinterpret_cast<int*>(sm + FwdSmem::FLAG) + 1;
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + FwdSmem::SLOT);
   float* bias = reinterpret_cast<float*>(sm + FwdSmem::BIAS);
-  if (warp == 0) tmem_alloc(slot, 256);
-  if (gt == 0) mbar_init(mbar, 1);
+  const uint32_t sRing = smem_u32(sm + FwdSmem::RING);
+  const int tiles = (n + 127) / 128;
+  // this CTA's tiles: blockIdx.x + i gridDim.x, i < my_tiles
+  const int my_tiles = (int)blockIdx.x < tiles ? (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const int n_chunks = my_tiles * kChunks;
+  auto load_chunk = [&](int seq) {
+    const int i = seq / kChunks, j = seq % kChunks;
+    const int sl = seq % kRing;
+    const int y = ((int)blockIdx.x + i * (int)gridDim.x) * 128;
+    mbar_expect_tx(full + sl, kChunkBytes);
+    if (map3d) {
+      // (8 columns, 128 rows, 4 column groups): the whole chunk in one copy
+      tma_load_3d(sRing + (uint32_t)sl * kChunkBytes, &tmX, 0, y, (kChunkK / 8) * j, full + sl);
+    } else {
+      for (int q = 0; q < kChunkK / 8; ++q)  // 8 columns x 128 rows (2 KB) per copy
+        tma_load_2d(sRing + (uint32_t)sl * kChunkBytes + 2048u * q, &tmX, kChunkK * j + 8 * q, y, full + sl);
+    }
+  };
+  if (warp == 0) tmem_alloc(slot, 512);
+  if (tid == 0) {
+    mbar_init(accb, 1);
+    mbar_init(accb + 1, 1);
+    for (int r = 0; r < kRing; ++r) mbar_init(full + r, 1);
+    *l1done = 0;
+    *issued = min(kRing, n_chunks);
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+    for (int q = 0; q < min(kRing, n_chunks); ++q) load_chunk(q);
+  }
   stage_weights(sm + FwdSmem::W1, Wb + kOffW1, kHid, kIn);
   stage_weights(sm + FwdSmem::W2, Wb + kOffW2, kHid, kHid);
   stage_weights(sm + FwdSmem::W3, Wb + kOffW3, kHid, kHid);
@@ -228,97 +325,137 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tcol = *slot + 128u * (uint32_t)g;  // this group's accumulator columns
-  unsigned char* act = sm + FwdSmem::ACT + (uint32_t)g * (128 * kHid * 2);
-  const uint32_t sAct = smem_u32(act);
+  const uint32_t tacc = *slot + 256u * (uint32_t)g;  // this group's accumulator columns
+  const uint32_t thid = tacc + 128u;                  // and its hidden activation (64 columns of BF16 pairs)
   const uint32_t sW[4] = {smem_u32(sm + FwdSmem::W1), smem_u32(sm + FwdSmem::W2), smem_u32(sm + FwdSmem::W3),
                           smem_u32(sm + FwdSmem::W4)};
   const int quarter = wl & 3, cgrp = wl >> 2;
-  const uint32_t lane_base = tcol + ((uint32_t)(32 * quarter) << 16);
+  const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
   uint32_t phase = 0;
   bool ok = true;
-  const int tiles = (n + 127) / 128;
-  // the MMAs of one layer (or one K half of layer 1) from this group's
-  // buffer, then wait for them; false when the wait gave up
-  auto run_mma = [&](int layer, int s0, uint32_t bsbo, int N, bool accumulate_first) -> bool {
-    fence_async_smem();
-    tc_fence_before();
-    group_sync(g);
-    if (gt == 0) {
-      tc_fence_after();
-      for (int s = 0; s < 8; ++s)
-        mma_bf16(tcol, sdesc(sAct + 256u * s, 128u, 2048u), sdesc(sW[layer] + 256u * (s0 + s), 128u, bsbo),
-                 idesc_bf16(128, N), (accumulate_first || s > 0) ? 1u : 0u);
-      mma_commit(mbar);
+  bool pending = false;  // the group's issuer committed MMAs nobody has waited for
+  // Every wait's outcome is made uniform over the group (a barrier with an
+  // AND) before any branch on it, so all 256 threads pass the same barriers.
+  auto wait_acc = [&]() -> bool {
+    const bool w = group_all(g, mbar_wait(accb, phase));
+    if (w) {
+      phase ^= 1u;
+      pending = false;
     }
-    const bool w = mbar_wait(mbar, phase);
-    phase ^= 1u;
     tc_fence_after();
     return w;
   };
-  for (int tile = blockIdx.x + g * gridDim.x; tile < tiles && ok; tile += 2 * gridDim.x) {
-    const int m0 = tile * 128;
-    // layer 1: the input in two K halves of 128 columns
-    for (int h = 0; h < 2 && ok; ++h) {
-      for (int e = gt; e < 128 * (kHid / 8); e += kGroupThreads) {
-        const int r = e / (kHid / 8), c = e % (kHid / 8);
-        const bool valid = m0 + r < n;
-        cp_async16(sAct + kmaj_off(r, c * 8, kHid),
-                   valid ? (const void*)(X + (size_t)(m0 + r) * kIn + kHid * h + c * 8) : (const void*)X, valid);
+  for (int i = g; i < my_tiles && ok; i += 2) {
+    const int m0 = ((int)blockIdx.x + i * (int)gridDim.x) * 128;
+    // layer 1: the tile's 8 input chunks from the ring (the accumulator is
+    // free: the group finished the previous tile)
+    bool good = true;
+    if (gt == 0) {
+      long w = 0;
+      while (*l1done < i && w < kWaitLimit) ++w;
+      good = *l1done >= i;
+      bool any = false;
+      for (int j = 0; j < kChunks && good; ++j) {
+        const int seq = i * kChunks + j, sl = seq % kRing;
+        good = mbar_wait(full + sl, (uint32_t)((seq / kRing) & 1));
+        if (!good) break;
+        if (j == 0) tc_fence_after();
+#pragma unroll
+        for (int s2 = 0; s2 < kChunkK / 16; ++s2)
+          mma_bf16(tacc, sdesc(sRing + (uint32_t)sl * kChunkBytes + 4096u * s2, 2048u, 128u),
+                   sdesc(sW[0] + 256u * (2 * j + s2), 128u, (kIn / 8) * 128u), idesc_bf16(128, kHid),
+                   (j > 0 || s2 > 0) ? 1u : 0u);
+        any = true;
       }
-      cp_async_commit();
-      cp_async_wait_all();
-      ok = run_mma(0, 8 * h, (kIn / 8) * 128u, kHid, h > 0);
+      if (any) {
+        mma_commit(accb);  // also after a failed wait: the exit path waits for it
+        pending = true;
+      }
+    }
+    if (!(ok = group_all(g, good))) break;
+    if (!(ok = wait_acc())) break;
+    if (gt == 0) {
+      // the chunks of this tile are consumed: load the ones kRing further on
+      // into their slots, then let the next tile's layer 1 start
+      for (int j = 0; j < kChunks; ++j) {
+        const int seq = i * kChunks + j + kRing;
+        if (seq < n_chunks) load_chunk(seq);
+      }
+      atomicMax(issued, min(i * kChunks + kChunks + kRing, n_chunks));
+      __threadfence_block();
+      *l1done = i + 1;
     }
     const int row = 32 * quarter + lane;
     const int grow = m0 + row;
-    for (int layer = 0; layer < 4 && ok; ++layer) {
-      if (layer > 0) ok = run_mma(layer, 0, (kHid / 8) * 128u, layer == 3 ? kOutP : kHid, false);
-      if (!ok) break;
+    for (int layer = 0; layer < 4; ++layer) {
+      if (layer > 0) {
+        // the hidden activation is in tensor memory (every thread waited for
+        // its stores) and the accumulator has been read
+        tmem_wait_st();
+        tc_fence_before();
+        group_sync(g);
+        if (gt == 0) {
+          tc_fence_after();
+          const int N = layer == 3 ? kOutP : kHid;
+          for (int s = 0; s < kHid / 16; ++s)
+            mma_bf16_ta(tacc, thid + 8u * s, sdesc(sW[layer] + 256u * s, 128u, (kHid / 8) * 128u), idesc_bf16(128, N),
+                        s > 0 ? 1u : 0u);
+          mma_commit(accb);
+          pending = true;
+        }
+        if (!(ok = wait_acc())) break;
+      }
       if (layer < 3) {
-        // bias + GELU -> the next layer's operand in this group's buffer
-        // (the MMAs that read it have completed)
+        // bias + GELU -> the next layer's A operand in tensor memory
         for (int half = 0; half < 2; ++half) {
           const int c0 = 64 * cgrp + 32 * half;
           float v[32];
-          tmem_ld32(lane_base + (uint32_t)c0, v);
+          tmem_ld32(tacc + lane_off + (uint32_t)c0, v);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += bias[layer * kHid + c0 + j];
           if (Zs && grow < n)
             for (int j = 0; j < 32; ++j) Zs[((size_t)layer * n + grow) * kHid + c0 + j] = v[j];
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = gelu(v[j]);
+          uint32_t pk[16];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            uint4 pk = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
-                                  pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-            *reinterpret_cast<uint4*>(act + kmaj_off(row, c0 + 8 * q, kHid)) = pk;
-            if (Hs && grow < n)
-              *reinterpret_cast<uint4*>(Hs + ((size_t)layer * n + grow) * kHid + c0 + 8 * q) = pk;
-          }
+          for (int q = 0; q < 16; ++q) pk[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
+          tmem_st16(thid + lane_off + (uint32_t)(c0 / 2), pk);
+          if (Hs && grow < n)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<uint4*>(Hs + ((size_t)layer * n + grow) * kHid + c0 + 8 * q) =
+                  make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
       } else if (cgrp == 0) {
         float v[16];
-        tmem_ld16(lane_base, v);
+        tmem_ld16(tacc + lane_off, v);
         if (grow < n)
           for (int j = 0; j < kOut; ++j) out[(size_t)grow * kOut + j] = v[j] + bias[3 * kHid + j];
       }
     }
-    // the next tile's input overwrites the buffer and the accumulator: every
-    // warp of the group is done with both
+    if (!ok) break;
+    // the next tile's layer 1 overwrites the accumulator: every warp of the
+    // group is done with it
     tc_fence_before();
     group_sync(g);
   }
-  if (!ok) {
-    if (gt == 0) atomicExch(err, kErrTimeout);
-    (void)mbar_wait(mbar, phase ^ 1u);  // give an outstanding commit one more bounded chance
+  if (!ok && gt == 0) {
+    atomicExch(err, kErrTimeout);
+    if (pending) (void)mbar_wait(accb, phase);  // give an outstanding commit one more bounded chance
   }
-  cp_async_wait_all();  // no copy in flight when the CTA leaves
   tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    // no copy may be in flight when the CTA leaves: the last kRing chunks
+    // issued occupy distinct slots, so each slot's latest phase is theirs
+    const int hi = *issued;
+    for (int seq = max(0, hi - kRing); seq < hi; ++seq) (void)mbar_wait(full + seq % kRing, (uint32_t)((seq / kRing) & 1));
+  }
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(*slot, 256);
+    tmem_dealloc(*slot, 512);
   }
 }
 
@@ -673,17 +810,71 @@ int ensure_ws(dmr_mlp* M, int n) {
   return DMR_OK;
 }
 
-void launch_forward(dmr_mlp* M, const __nv_bfloat16* X, int n, float* out, float* Zs, __nv_bfloat16* Hs) {
+// The driver's tensor-map encoder, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// X BF16 [n][256] as a tensor map whose boxes land in the ring's layout:
+// 3-D (column within a group of 8, row, group of 8 columns; strides 512 and
+// 16 bytes), box 8 x 128 x 4 = one chunk; where the driver does not take
+// that view, 2-D (column, row), box 8 x 128, four per chunk.  Rows past n
+// read as 0.
+int make_input_map(const __nv_bfloat16* X, int n, CUtensorMap* map, int* map3d) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return set_error(DMR_ECUDA, "mlp: cuTensorMapEncodeTiled not available");
+  if (((uintptr_t)X & 15u) != 0) return set_error(DMR_EINVAL, "mlp: X must be 16-byte aligned");
+  {
+    const cuuint64_t dims[3] = {8, (cuuint64_t)n, (cuuint64_t)kIn / 8};
+    const cuuint64_t strides[2] = {(cuuint64_t)kIn * 2, 16};
+    const cuuint32_t box[3] = {8, 128, (cuuint32_t)kChunkK / 8};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)X, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+        CUDA_SUCCESS) {
+      *map3d = 1;
+      return DMR_OK;
+    }
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)kIn, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)kIn * 2};
+  const cuuint32_t box[2] = {8, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)X, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(DMR_ECUDA, "mlp: input tensor map rejected (" + std::to_string((int)r) + ")");
+  *map3d = 0;
+  return DMR_OK;
+}
+
+int launch_forward(dmr_mlp* M, const __nv_bfloat16* X, int n, float* out, float* Zs, __nv_bfloat16* Hs) {
   static bool once = false;
   if (!once) {
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FwdSmem::TOTAL);
     once = true;
   }
+  CUtensorMap map;
+  int map3d = 0;
+  const int rc = make_input_map(X, n, &map, &map3d);
+  if (rc) return rc;
   int tiles = (n + 127) / 128;
   // two tiles in flight per CTA once there are more tiles than SMs; with
   // fewer (training batches) one tile per CTA, on more SMs
   int grid = tiles <= M->n_sm ? tiles : std::min((tiles + 1) / 2, M->n_sm);
-  k_mlp_forward<<<grid, kFwdThreads, FwdSmem::TOTAL, M->st>>>(X, n, M->Wb, M->P, out, Zs, Hs, M->err);
+  k_mlp_forward<<<grid, kFwdThreads, FwdSmem::TOTAL, M->st>>>(map, map3d, n, M->Wb, M->P, out, Zs, Hs, M->err);
+  return DMR_OK;
 }
 
 // SplitMix64, a published counter-based generator, for the initial weights.
@@ -790,7 +981,8 @@ int dmr_mlp_features(dmr_problem* p, const double* coords, int C, void* X) {
 
 int dmr_mlp_forward(dmr_mlp* M, const void* X, int n, float* out) {
   if (!M || !X || !out || n < 1) return set_error(DMR_EINVAL, "bad mlp forward arguments");
-  launch_forward(M, (const __nv_bfloat16*)X, n, out, nullptr, nullptr);
+  int rc = launch_forward(M, (const __nv_bfloat16*)X, n, out, nullptr, nullptr);
+  if (rc) return rc;
   if (cudaGetLastError() != cudaSuccess) return set_error(DMR_ECUDA, "mlp forward launch");
   return check_err(M);
 }
@@ -806,7 +998,7 @@ int dmr_mlp_train_step(dmr_mlp* M, const void* Xv, const float* Y, int n, float 
   const __nv_bfloat16* X = (const __nv_bfloat16*)Xv;
   cudaStream_t st = M->st;
   cudaMemsetAsync(M->loss, 0, sizeof(double), st);
-  launch_forward(M, X, n, M->out, M->Zs, M->Hs);
+  if ((rc = launch_forward(M, X, n, M->out, M->Zs, M->Hs))) return rc;
   k_nll_grad<<<(n + 127) / 128, 128, 0, st>>>(M->out, Y, n, M->dZ4, M->loss);
   float* G = M->G;
   const __nv_bfloat16* W = M->Wb;
