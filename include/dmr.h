@@ -304,10 +304,12 @@ int dmr_mlp_params(dmr_mlp* mlp, float* get, const float* set);
 /* Features of every (candidate, point) of coords (device [C][2][3][P]) into
  * X (device BF16 [C*P][256]). */
 int dmr_mlp_features(dmr_problem* p, const double* coords, int C, void* X);
-/* out (device FP32 [n][6]) = network(X) for X device BF16 [n][256]. */
+/* out (device FP32 [n][6]) = network(X) for X device BF16 [n][256], X
+ * 16-byte aligned (it is read by the tensor memory accelerator; DMR_EINVAL
+ * otherwise). */
 int dmr_mlp_forward(dmr_mlp* mlp, const void* X, int n, float* out);
 /* Gaussian negative log-likelihood of targets Y (device FP32 [n][3]) on
- * batch X; gradient by backpropagation on the tensor cores; if lr > 0 one
+ * batch X (16-byte aligned, as for dmr_mlp_forward); gradient by backpropagation on the tensor cores; if lr > 0 one
  * Adam step.  loss_out (host, may be NULL) = mean loss before the step;
  * grad_out (host FP32 [n_params], may be NULL) = the gradient.  With both
  * NULL the call only enqueues the step on the network's stream and returns

@@ -722,11 +722,8 @@ template <typename TA, typename TB>
 void gemm(int M, int N, int K, const TA* A, long sam, long sak, const TB* B, long sbn, long sbk, float* C, long scm,
           long scn, int acc, int* err, float* ws, int n_sm, cudaStream_t st) {
   const size_t smem = 2 * (16384 + 32768) + 32;
-  static bool once = false;
-  if (!once) {
-    cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    once = true;
-  }
+  // per launch: the attribute belongs to the current device
+  cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int mt = (M + 127) / 128, chunks = (K + 63) / 64;
   int S = std::min(std::max(1, (2 * n_sm + mt - 1) / mt), chunks);
   if ((size_t)S * M * N > kSplitWs) S = std::max(1, (int)(kSplitWs / ((size_t)M * N)));
@@ -860,11 +857,8 @@ int make_input_map(const __nv_bfloat16* X, int n, CUtensorMap* map, int* map3d) 
 }
 
 int launch_forward(dmr_mlp* M, const __nv_bfloat16* X, int n, float* out, float* Zs, __nv_bfloat16* Hs) {
-  static bool once = false;
-  if (!once) {
-    cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FwdSmem::TOTAL);
-    once = true;
-  }
+  // per launch: the attribute belongs to the current device
+  cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FwdSmem::TOTAL);
   CUtensorMap map;
   int map3d = 0;
   const int rc = make_input_map(X, n, &map, &map3d);

@@ -149,3 +149,17 @@ def test_features_match_scipy_patches():
                         want.append(ndimage.map_coordinates(img, [[q[2]], [q[1]], [q[0]]], order=1, mode="nearest")[0])
         want = np.array(want)
         assert np.allclose(X[row, :250], want, atol=1e-2, rtol=1e-2)
+
+
+def test_forward_rejects_unaligned_input():
+    """The input is read by TMA, whose base address must be 16-byte aligned:
+    a view starting 2 bytes into a buffer is refused on the host (no launch)."""
+    import torch
+
+    m = dmr.MLP(seed=3)
+    flat = torch.zeros(1 + 4 * 256, dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(dmr.DmrError):
+        m.forward(flat[1:].view(4, 256))
+    ok = m.forward(flat[:4 * 256].view(4, 256))  # the aligned view still runs
+    assert tuple(ok.shape) == (4, 6)
+    m.close()
