@@ -284,9 +284,9 @@ int dmr_refine(const double* coarse, int n_cand, const int* m, double* fine, voi
  * every coordinate add nothing.  *out receives the volume. */
 int dmr_hypervolume(const double* pts, int n, int d, const double* ref, double* out);
 
-/* Learned proposal (a network the paper does not have; the method's own
- * proposals stay the judge: every proposal is still scored by the
- * evaluator).  An MLP 256 -> 128 -> 128 -> 128 -> 6 with GELU (tanh form) maps features
+/* Learned proposal (a network the paper does not have; its samples are
+ * mixed into the method's own proposals, and every proposal is still scored
+ * by the evaluator).  An MLP 256 -> 128 -> 128 -> 128 -> 6 with GELU (tanh form) maps features
  * of a (candidate, point) -- 5x5x5 trilinear patches of both images around
  * the source and target point, the correspondence offset and the position --
  * to the mean (3) and log-variance (3) of a Gaussian displacement of the
