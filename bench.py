@@ -51,6 +51,12 @@ FALLBACK_HBM_GBS = 6800.0
 # the current kernel (1-pass metrics, caches not flushed) summarised under
 # profiles/, per (workload, storage); None for workloads without one.
 FAST_PASS_DRAM_BYTES = {("batch64", "f32"): 23.94e9, ("ct", "f32"): 2.498e9, ("ellipsoid64", "f32"): 5.3e6}
+# Instruction-issue utilisation of the fast raster pass (smsp__issue_active,
+# share of cycles in which a warp instruction issued), from the ncu captures
+# of the current kernel summarised under profiles/: the resource that binds
+# it (its ALU fraction counts only the 37 sampling operations per executed
+# sample, not the rasterisation instructions).
+FAST_PASS_ISSUE_ACTIVE = {("batch64", "f32"): 0.798, ("ct", "f32"): 0.782}
 
 
 def reduce_over_ranks(total_s, samples, dist, device):
@@ -320,7 +326,8 @@ def run_batch(args):
                 "frac_on_counted_samples": counted_step * ALG_OPS_PER_SAMPLE / raster_s / 1e12 / alu_peak,
                 "touched_bytes_frac_of_hbm": value * 2 * bpv / 1e9 / hbm,
                 "touched_bytes_frac_of_hbm_executed": executed_step / (total_s / args.steps) * 2 * bpv / 1e9 / hbm,
-                "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind}
+                "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind,
+                "issue_active_ncu": FAST_PASS_ISSUE_ACTIVE.get(("batch64", args.storage))}
     launches = plan.launches
     plan.close()
     bt.close()
@@ -954,6 +961,7 @@ def main():
     traffic = FAST_PASS_DRAM_BYTES.get((args.workload, args.storage))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-op/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
+                "issue_active_ncu": FAST_PASS_ISSUE_ACTIVE.get((args.workload, args.storage)),
                 "traffic_unit": "DRAM bytes per fast raster-pass launch (one wave), ncu",
                 "kernel": "k_raster (rasterise + map + trilinear sample + SSD)",
                 "ops_per_sample": ALG_OPS_PER_SAMPLE, "basis": "executed samples",
