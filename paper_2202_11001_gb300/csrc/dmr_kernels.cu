@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(128, 4) k_setup(const DevProblem* __restrict__
     const float* phi = phi_;
     int O[3], Op[3], B0[3], B1[3];
     int L = 1;
+    float La[3];  // per-axis extent: 0 <= q_a <= La - 1 for the box's voxels
     for (int a = 0; a < 3; ++a) {
       float cl = ceilf(lo[a]), fh = floorf(hi[a]);
       B0[a] = cl < 0.f ? 0 : (int)fminf(cl, (float)n[a]);
@@ -497,6 +498,7 @@ __global__ void __launch_bounds__(128, 4) k_setup(const DevProblem* __restrict__
       O[a] = (int)fmaxf(fminf(floorf(lo[a]), (float)n[a]), -2.0f);
       Op[a] = (int)fmaxf(fminf(floorf(plo[a]), (float)np[a]), -2.0f);
       L = max(L, B1[a] - O[a] + 1);
+      La[a] = (float)max(1, B1[a] - O[a] + 1);
     }
     R4[1] = make_int4(B0[0], B0[1], B0[2], 0);
     R4[2] = make_int4(B1[0], B1[1], B1[2], 0);
@@ -520,14 +522,17 @@ __global__ void __launch_bounds__(128, 4) k_setup(const DevProblem* __restrict__
     // of a face cross product, of the face opposite vertex m = 1, 2, 3, and
     // -(rr[0] + rr[1] + rr[2]) that of the face opposite vertex 0; within a
     // few 2^-53 U W of the oracle's normals) and FP64 offsets B = -n.(a - O),
-    // each rounded once to FP32.  At a voxel q = p - O of the box
-    // (0 <= q < L), h(q) = fl(A.q + B) differs from the FP64 predicate by at
-    // most eps (an L + |B|) from rounding A and B, plus 3 eps (1 + eps)^3
-    // (an L + |B|) from the three roundings of the evaluation (each partial
-    // sum is at most (1 + eps)(an L + |B|); eps = 2^-24), plus 1.5e-14
-    // (U W + an)(L + V) for the FP64 predicate's own rounding.  The margin
-    // takes 5 eps (an L + |B|) for the FP32 part: a quarter above its bound,
-    // which covers the rounding of an, |B| and of the margin itself.
+    // each rounded once to FP32.  At a point q = p - O with |q_a| <= La_a
+    // on every axis (the box's voxels and the one just outside each row end,
+    // the only points the spans evaluate), |A.q| <= aL = sum_a |A_a| La_a,
+    // and h(q) = fl(A.q + B) differs from the FP64 predicate by at most
+    // eps (aL + |B|) from rounding A and B, plus 3 eps (1 + eps)^3 (aL + |B|)
+    // from the three roundings of the evaluation (each partial sum is at most
+    // (1 + eps)(aL + |B|); eps = 2^-24), plus 1.5e-14 (U W + an)(L + V) for
+    // the FP64 predicate's own rounding (an = sum_a |A_a|, L = max_a La_a).
+    // The margin takes 5 eps (aL + |B|) for the FP32 part: a quarter above
+    // its bound, which covers the rounding of aL, |B| and of the margin
+    // itself.  (The landmark test adds terms in |q| of its own.)
     const double N0[3] = {-((rr[0][0] + rr[1][0]) + rr[2][0]), -((rr[0][1] + rr[1][1]) + rr[2][1]),
                           -((rr[0][2] + rr[1][2]) + rr[2][2])};
     const uint32_t fp = pr.fperm[t];
@@ -546,7 +551,8 @@ __global__ void __launch_bounds__(128, 4) k_setup(const DevProblem* __restrict__
       const float Ax = d2f(nx), Ay = d2f(ny), Az = d2f(nz), Bp = d2f(Bd);
       axf[f] = Ax;
       const float an = fabsf(Ax) + fabsf(Ay) + fabsf(Az);
-      const float mu = (5.0f / 16777216.0f) * (an * Lf + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
+      const float aL = fabsf(Ax) * La[0] + fabsf(Ay) * La[1] + fabsf(Az) * La[2];
+      const float mu = (5.0f / 16777216.0f) * (aL + fabsf(Bp)) + 1.5e-14f * (UW + an) * (Lf + V) + 1e-30f;
       *reinterpret_cast<float4*>(&R.fa[f][0]) = make_float4(Ax, Ay, Az, Bp);
       // fm: margin, 1/A.x, margin growth per voxel of |p - O| (landmarks),
       // and the bound on |A.x - s n_x| beyond FP32 rounding (the fused and
